@@ -1,0 +1,139 @@
+"""Pins of the oracle's micro solve and averaging (Sections 2.2-2.3, 3.1, 4.1-4.2).
+
+* HeunP keeps |m| = 1 on the interior and m = m_init on the Dirichlet ring.
+* The exchange energy decays monotonically for alpha > 0 under the dt rule,
+  and the solve blows up above the HeunP stability limit (eq. Cstab).
+* HeunP is second order in dt (Section 3.1).
+* Physics: H_avg approaches div(grad m_init(0) A^H) (Theorem 2) with A^H from
+  closed forms: the 1D harmonic mean (EX1 coefficient) with the paper's 1D
+  parameters (Section 5, locally periodic example: mu = 3.9 eps, mu' = 8 eps,
+  eta ~ eps^2, alpha = 1.2) and the separable (EX3) coefficient in 2D.
+* Invariants: constant M gives H_avg = 0; rotating all macro vectors rotates H_avg.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hmm_oracle as O
+
+
+def _one_box(cfg, p, M0):
+    geo = O.box_geometry(cfg, p)
+    mi = O.micro_initial(cfg, M0, geo)[None]
+    af = [a[None] for a in O.face_coefficients(cfg, geo)]
+    N, r = geo["N"], geo["r"]
+    W1 = O.space_weights(N, geo["dx"], geo["mu"], cfg.px, cfg.qx)[r:N - r]
+    Wd = W1
+    for _ in range(cfg.dim - 1):
+        Wd = np.multiply.outer(Wd, W1)
+    w = O.time_weights(cfg.micro_steps, cfg.pt, cfg.qt)
+    return geo, mi, af, Wd, w
+
+
+@pytest.mark.parametrize("name,over", [("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=120)),
+                                       ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=60))])
+def test_norm_ring_and_energy(name, over):
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    geo, mi, af, Wd, w = _one_box(cfg, 3, M0)
+    S, m, E, nd = O.micro_solve(mi, af, geo["dx"], geo["dt"], cfg.micro_steps, cfg.alpha_micro,
+                                Wd, w, cfg.stencil_order, trace=True)
+    assert nd.max() < 1e-14
+    r = geo["r"]
+    ring = np.ones(m.shape, bool)
+    ring[(Ellipsis,) + tuple(slice(r, geo["N"] - r) for _ in range(cfg.dim))] = False
+    assert np.array_equal(m[ring], mi[ring])
+    E = E[:, 0]
+    assert np.all(np.diff(E) <= 1e-13 * E[0]), "energy must decay monotonically for alpha > 0"
+    assert E[-1] < E[0]
+
+
+def test_unstable_above_heun_limit():
+    for safety, stable in ((0.8, True), (1.3, False)):
+        cfg = W.config("c1_1d", n_macro=(16, 1, 1), box_n=81, micro_steps=300, dt_safety=safety)
+        M0 = W.initial_field(cfg)
+        geo, mi, af, Wd, w = _one_box(cfg, 3, M0)
+        _, _, E, _ = O.micro_solve(mi, af, geo["dx"], geo["dt"], cfg.micro_steps, cfg.alpha_micro,
+                                   Wd, w, 4, trace=True)
+        grow = E.max() / E[0]
+        assert (grow <= 1.0 + 1e-12) if stable else (grow > 10.0), (safety, grow)
+
+
+def test_heun_second_order_in_time():
+    cfg = W.config("c1_1d", n_macro=(16, 1, 1), box_n=41, micro_steps=10)
+    M0 = W.initial_field(cfg)
+    geo, mi, af, Wd, _ = _one_box(cfg, 5, M0)
+    T = 40 * geo["dt"]
+
+    def final(nsteps):
+        w = np.zeros(nsteps + 1)
+        _, m, _, _ = O.micro_solve(mi, af, geo["dx"], T / nsteps, nsteps, cfg.alpha_micro, Wd, w, 4, trace=True)
+        return m
+
+    ref = final(40 * 32)
+    errs = [np.abs(final(40 * s) - ref).max() for s in (1, 2, 4)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8) and np.all(rates < 2.3), (errs, rates)
+
+
+def _physics_1d(eps, points):
+    K, mup, mu, eta = 20, 8.0, 3.9, 1.0
+    cfg = W.config("c1_1d", eps=eps, pts_per_eps=K, box_n=int(2 * mup * K) + 1, mu_over_eps=mu)
+    dt = O.micro_dt(cfg, eps / K)
+    cfg = cfg.replace(micro_steps=int(np.ceil(eta * eps * eps / dt)))
+    M0 = W.initial_field(cfg)
+    H = O.micro_batch(cfg, M0, points=points)
+    errs = []
+    for j, p in enumerate(points):
+        _, _, Q2 = O.q_derivatives_at_centre(cfg, M0, p)
+        tgt = O.homogenised_target(np.array([[np.sqrt(0.75)]]), Q2)
+        errs.append(np.linalg.norm(H[:, j] - tgt) / np.linalg.norm(tgt))
+    return max(errs)
+
+
+def test_physics_1d_harmonic_mean():
+    """a = 1 + 0.5 sin(2 pi y): A^H = (int 1/a)^-1 = sqrt(3)/2 (EX1). E_avg ~ 1e-3 here."""
+    assert _physics_1d(1 / 100, [0, 5, 17, 40]) < 5e-3
+
+
+def test_physics_2d_separable_closed_form():
+    """(EX3) coefficient: A^H = 1.1 sqrt(1.1^2 - 0.25) I; (EX2) initial data."""
+    terms = [W._term(0.55, W._sin(0)), W._term(0.55, W._sin(1)), W._term(0.25, W._sin(0), W._sin(1))]
+    eps, K = 1 / 400, 8
+    cfg = W.HMMConfig(dim=2, n_macro=(24, 24, 1), alpha=0.01, alpha_micro=1.0, c0=1.21, terms=terms,
+                      eps=eps, box_n=97, pts_per_eps=K, micro_steps=10, mu_over_eps=4.2)
+    dt = O.micro_dt(cfg, eps / K)
+    cfg = cfg.replace(micro_steps=int(np.ceil(0.5 * eps * eps / dt)))
+    X1, X2 = np.meshgrid(*W.macro_coords(cfg), indexing="ij")
+    M0 = W.ex2_initial(X1, X2).reshape(3, -1)
+    p = 7 * 24 + 3
+    H = O.micro_batch(cfg, M0, points=[p])[:, 0]
+    _, _, Q2 = O.q_derivatives_at_centre(cfg, M0, p)
+    tgt = O.homogenised_target(1.1 * np.sqrt(0.96) * np.eye(2), Q2)
+    assert np.linalg.norm(H - tgt) / np.linalg.norm(tgt) < 2e-2
+
+
+def test_constant_macro_field_gives_zero():
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=30)
+    M0 = np.tile(np.array([0.6, 0.0, 0.8])[:, None], (1, 64))
+    H = O.micro_batch(cfg, M0, points=[0, 9, 63])
+    # m_init is constant up to rounding (~1e-16), amplified by a/dx^2 ~ 1e7 before averaging
+    assert np.abs(H).max() < 1e-8
+
+
+def test_rotation_equivariance():
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=30)
+    M0 = W.initial_field(cfg)
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    R = R @ np.array([[1, 0, 0], [0, np.cos(0.3), -np.sin(0.3)], [0, np.sin(0.3), np.cos(0.3)]])
+    pts = [0, 13, 40]
+    H = O.micro_batch(cfg, M0, points=pts)
+    HR = O.micro_batch(cfg, R @ M0, points=pts)
+    np.testing.assert_allclose(HR, R @ H, rtol=1e-9, atol=1e-9 * np.abs(H).max())
+
+
+def test_ll_rhs_hand_value():
+    """f(e_z, e_x) = -e_z x e_x - alpha e_z x (e_z x e_x) = (alpha, -1, 0)."""
+    f = O.ll_rhs(np.array([0.0, 0.0, 1.0]), np.array([1.0, 0.0, 0.0]), 0.3)
+    np.testing.assert_allclose(f, [0.3, -1.0, 0.0], atol=1e-15)

@@ -1,0 +1,281 @@
+"""Seeded synthetic inputs for the HMM micro-problem path.
+
+This module is shared by the CUDA path's tests/bench and by the oracle. It holds
+problem *descriptions* (parameters, coefficient terms) and seeded generators of
+macro magnetisation fields. It holds none of the method's arithmetic: no
+kernels, weights, interpolation, stencils, time stepping or averaging.
+
+Workloads follow the paper's problem statement (Section 2.1, eq. prob): a
+periodic domain [0, L]^d, a coefficient a^eps that oscillates on the scale eps,
+damping alpha and unit-length initial data (assumption A3). The named
+configurations below carry the shapes, sizes and value distributions of the
+paper's examples (Section 2.4 EX1-EX3, Section 5) at the sizes of the
+benchmark table in the design doc.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "CoefTerm", "HMMConfig", "config", "CONFIG_NAMES", "fourier_field",
+    "ex1_initial", "ex2_initial", "c1_initial", "uneven_eps_and_n",
+    "macro_coords",
+]
+
+# Coefficient factor kinds and variable scales (per axis of a term).
+KIND_ONE, KIND_SIN, KIND_COS = 0, 1, 2
+SCALE_FAST, SCALE_SLOW = 0, 1
+
+
+@dataclasses.dataclass
+class CoefTerm:
+    """One term amp * prod_k g_k(2*pi*omega_k*s_k + phase_k) of a(x).
+
+    g_k is 1, sin or cos (``kind``); s_k = x_k/eps (fast variable, ``scale`` 0)
+    or s_k = x_k (slow variable, ``scale`` 1). Axes beyond the problem's
+    dimension must have kind 1 (the factor 1).
+    """
+    amp: float
+    kind: Sequence[int] = (KIND_ONE, KIND_ONE, KIND_ONE)
+    scale: Sequence[int] = (SCALE_FAST, SCALE_FAST, SCALE_FAST)
+    omega: Sequence[float] = (1.0, 1.0, 1.0)
+    phase: Sequence[float] = (0.0, 0.0, 0.0)
+
+
+@dataclasses.dataclass
+class HMMConfig:
+    """Parameters of one HMM problem (the fields of the C struct hmm_params).
+
+    dim, n_macro, L          periodic macro domain [0, L]^dim, n_macro points/axis
+    alpha, alpha_micro       macro damping and artificial micro damping
+    dt_macro                 macro time step (<= 0: library/oracle default)
+    c0, terms                a(x) = c0 + sum(terms)
+    eps / eps_field          uniform eps or one eps per macro point (C order)
+    box_n / box_n_field      micro nodes per axis (ring included), uniform or per point
+    pts_per_eps              K: micro grid spacing dx = eps/K
+    mu_over_eps              averaging half-width mu/eps (<= 0: mu = 0.8*mu')
+    micro_steps              M: micro time steps per micro problem (eta = M*dt)
+    dt_safety                micro dt as a fraction of the HeunP stability limit
+    px, qx, pt, qt           kernel parameters of K in K^{px,qx}, K0 in K0^{pt,qt}
+    interp_order             2k of the normalised interpolation Q_[2k]
+    stencil_order            2 or 4
+    precision                0: plain FP64 method, 1: batched FP32 form
+    """
+    dim: int
+    n_macro: Sequence[int]
+    alpha: float
+    alpha_micro: float
+    c0: float
+    terms: List[CoefTerm]
+    eps: float
+    box_n: int
+    pts_per_eps: float
+    micro_steps: int
+    L: float = 1.0
+    dt_macro: float = 0.0
+    eps_field: Optional[np.ndarray] = None
+    box_n_field: Optional[np.ndarray] = None
+    mu_over_eps: float = 0.0
+    dt_safety: float = 0.8
+    px: int = 3
+    qx: int = 7
+    pt: int = 3
+    qt: int = 7
+    interp_order: int = 4
+    stencil_order: int = 4
+    precision: int = 0
+    name: str = ""
+
+    @property
+    def n_points(self) -> int:
+        return int(np.prod(list(self.n_macro)[: self.dim]))
+
+    def replace(self, **kw) -> "HMMConfig":
+        return dataclasses.replace(self, **kw)
+
+
+def macro_coords(cfg: HMMConfig) -> List[np.ndarray]:
+    """Macro grid coordinates x_i = i*DX per axis (x_0 = 0)."""
+    return [np.arange(n) * (cfg.L / n) for n in list(cfg.n_macro)[: cfg.dim]]
+
+
+def _grid(cfg: HMMConfig):
+    xs = macro_coords(cfg)
+    return np.meshgrid(*xs, indexing="ij")
+
+
+# --------------------------------------------------------------------------
+# Seeded initial data
+# --------------------------------------------------------------------------
+
+def fourier_field(cfg: HMMConfig, seed: int, kmax: int = 4, sigma: float = 0.5,
+                  offset=(0.3, 0.2, 0.9), min_norm: float = 0.25) -> np.ndarray:
+    """Normalised smooth random Fourier field on the macro grid, (3, *n_macro).
+
+    m~_c(x) = o_c + sum_{0<|k|<=kmax} sigma/(1+|k|^2) (A cos 2pi k.x + B sin 2pi k.x)
+    with A, B ~ N(0,1) drawn from numpy PCG64(seed); redrawn while
+    min |m~| < min_norm, then normalised pointwise (assumption A3).
+    """
+    d = cfg.dim
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rng_ks = [np.arange(-kmax, kmax + 1)] * d
+    ks = np.stack(np.meshgrid(*rng_ks, indexing="ij"), -1).reshape(-1, d)
+    norm2 = (ks ** 2).sum(1)
+    ks = ks[(norm2 > 0) & (norm2 <= kmax * kmax)]
+    amp = sigma / (1.0 + (ks ** 2).sum(1))
+    X = _grid(cfg)
+    shape = X[0].shape
+    for _attempt in range(64):
+        A = rng.standard_normal((3, len(ks)))
+        B = rng.standard_normal((3, len(ks)))
+        mt = np.empty((3,) + shape)
+        for c in range(3):
+            acc = np.full(shape, float(offset[c]))
+            for start in range(0, len(ks), 32):
+                kk = ks[start:start + 32]
+                ph = sum(kk[:, a].reshape((-1,) + (1,) * d) * X[a][None] for a in range(d))
+                ph = 2.0 * math.pi * ph
+                acc += np.tensordot(amp[start:start + 32] * A[c, start:start + 32], np.cos(ph), 1)
+                acc += np.tensordot(amp[start:start + 32] * B[c, start:start + 32], np.sin(ph), 1)
+            mt[c] = acc
+        nrm = np.sqrt((mt ** 2).sum(0))
+        if nrm.min() >= min_norm:
+            return mt / nrm
+    raise RuntimeError("fourier_field: could not draw a field with min |m| >= min_norm")
+
+
+def ex1_initial(x: np.ndarray) -> np.ndarray:
+    """(EX1) initial data of Section 2.4, normalised; x any shape -> (3, *x.shape)."""
+    mt = np.stack([
+        0.5 + np.exp(-0.1 * np.cos(2 * np.pi * (x - 0.32))),
+        0.5 + np.exp(-0.2 * np.cos(2 * np.pi * x)),
+        0.5 + np.exp(-0.1 * np.cos(2 * np.pi * (x - 0.75))),
+    ])
+    return mt / np.sqrt((mt ** 2).sum(0))
+
+
+def ex2_initial_unnormalised(x1: np.ndarray, x2: np.ndarray) -> np.ndarray:
+    """(EX2)/(EX3) m~ of Section 2.4 before normalisation."""
+    c = np.cos
+    tp = 2 * np.pi
+    return np.stack([
+        0.6 + np.exp(-0.3 * (c(tp * (x1 - 0.25)) + c(tp * (x2 - 0.12)))),
+        0.5 + np.exp(-0.4 * (c(tp * x1) + c(tp * (x2 - 0.4)))),
+        0.4 + np.exp(-0.2 * (c(tp * (x1 - 0.81)) + c(tp * (x2 - 0.73)))),
+    ])
+
+
+def ex2_initial(x1: np.ndarray, x2: np.ndarray) -> np.ndarray:
+    """(EX2)/(EX3) initial data of Section 2.4, normalised."""
+    mt = ex2_initial_unnormalised(x1, x2)
+    return mt / np.sqrt((mt ** 2).sum(0))
+
+
+def c1_initial(x: np.ndarray) -> np.ndarray:
+    """1D benchmark initial data: normalised (0.5+0.3 sin 2pi x, 0.4 cos 2pi x, 0.6)."""
+    mt = np.stack([0.5 + 0.3 * np.sin(2 * np.pi * x), 0.4 * np.cos(2 * np.pi * x),
+                   np.full_like(x, 0.6)])
+    return mt / np.sqrt((mt ** 2).sum(0))
+
+
+def uneven_eps_and_n(cfg: HMMConfig, K: float = 8.0, mu_prime: float = 0.015,
+                     nmin: int = 32, nmax: int = 96, step: int = 8):
+    """Locally varying eps and box sizes for the uneven-box workload.
+
+    1/eps_i = 250 + 150 sin(2 pi x1) cos(2 pi x2) in [100, 400]; with K points
+    per eps_i and a physical half-width mu' the box has
+    N_i = clamp(step*ceil(2 mu' K/eps_i/step), nmin, nmax) nodes per axis.
+    """
+    X = _grid(cfg)
+    inv = 250.0 + 150.0 * np.sin(2 * np.pi * X[0]) * np.cos(2 * np.pi * X[1])
+    eps = 1.0 / inv
+    n = step * np.ceil((2.0 * mu_prime * K / eps) / step)
+    n = np.clip(n, nmin, nmax).astype(np.int32)
+    return eps.reshape(-1).astype(np.float64), n.reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------
+
+def _sin(axis: int, scale: int = SCALE_FAST, omega: float = 1.0, phase: float = 0.0):
+    return axis, KIND_SIN, scale, omega, phase
+
+
+def _term(amp: float, *factors) -> CoefTerm:
+    kind = [KIND_ONE] * 3
+    scale = [SCALE_FAST] * 3
+    omega = [1.0] * 3
+    phase = [0.0] * 3
+    for (ax, k, s, w, p) in factors:
+        kind[ax], scale[ax], omega[ax], phase[ax] = k, s, w, p
+    return CoefTerm(amp, tuple(kind), tuple(scale), tuple(omega), tuple(phase))
+
+
+def _cos(axis: int, scale: int = SCALE_FAST, omega: float = 1.0, phase: float = 0.0):
+    return axis, KIND_COS, scale, omega, phase
+
+
+CONFIG_NAMES = ("c1_1d", "c2_2d", "c3_2d_uneven", "c4_3d", "c5_sweep")
+
+
+def config(name: str, **over) -> HMMConfig:
+    """Named workload configurations (sizes of the benchmark table).
+
+    c1_1d         1D, 64 macro points, eps=1/100, a=1+0.5 sin(2 pi y), alpha=0.1,
+                  N=201 (20 points per eps, width 10 eps), M=500, 4th-order stencil
+    c2_2d         2D, 128^2 macro grid, eps=1/200, a=1+0.5 sin(2pi y1) sin(2pi y2),
+                  alpha=0.05, N=64 (8 per eps), M=400
+    c3_2d_uneven  2D, 256^2, a=1.1+0.25 sin(2pi y1)cos(2pi y2)+0.25 sin(2pi x1)sin(2pi y2),
+                  eps_i in [1/400,1/100], N_i in 32..96, alpha=0.01, M=400, FP32 form
+    c4_3d         3D, 64^3, eps=1/100, a=1+0.5 prod sin(2pi y_k), alpha=0.1, N=32
+                  (6 per eps, mu=2 eps), M=300, FP32 form
+    c5_sweep      2D laminated a=1+0.9 sin(2pi y1), eps=1/400, K=10 (sizes set per point)
+    Micro damping alpha_micro = 1.2 (the paper's artificial damping) unless overridden.
+    """
+    if name == "c1_1d":
+        cfg = HMMConfig(dim=1, n_macro=(64, 1, 1), alpha=0.1, alpha_micro=1.2,
+                        c0=1.0, terms=[_term(0.5, _sin(0))], eps=1.0 / 100,
+                        box_n=201, pts_per_eps=20.0, micro_steps=500, name=name)
+    elif name == "c2_2d":
+        cfg = HMMConfig(dim=2, n_macro=(128, 128, 1), alpha=0.05, alpha_micro=1.2,
+                        c0=1.0, terms=[_term(0.5, _sin(0), _sin(1))], eps=1.0 / 200,
+                        box_n=64, pts_per_eps=8.0, micro_steps=400, name=name)
+    elif name == "c3_2d_uneven":
+        cfg = HMMConfig(dim=2, n_macro=(256, 256, 1), alpha=0.01, alpha_micro=1.2,
+                        c0=1.1, terms=[_term(0.25, _sin(0), _cos(1)),
+                                       _term(0.25, _sin(0, SCALE_SLOW), _sin(1))],
+                        eps=1.0 / 250, box_n=64, pts_per_eps=8.0, micro_steps=400,
+                        precision=1, name=name)
+    elif name == "c4_3d":
+        cfg = HMMConfig(dim=3, n_macro=(64, 64, 64), alpha=0.1, alpha_micro=1.2,
+                        c0=1.0, terms=[_term(0.5, _sin(0), _sin(1), _sin(2))],
+                        eps=1.0 / 100, box_n=32, pts_per_eps=6.0, mu_over_eps=2.0,
+                        micro_steps=300, precision=1, name=name)
+    elif name == "c5_sweep":
+        cfg = HMMConfig(dim=2, n_macro=(32, 32, 1), alpha=0.1, alpha_micro=1.0,
+                        c0=1.0, terms=[_term(0.9, _sin(0))], eps=1.0 / 400,
+                        box_n=64, pts_per_eps=10.0, micro_steps=400, name=name)
+    else:
+        raise KeyError(name)
+    cfg = dataclasses.replace(cfg, **over)
+    if name == "c3_2d_uneven" and cfg.eps_field is None:
+        eps, n = uneven_eps_and_n(cfg)
+        cfg = dataclasses.replace(cfg, eps_field=eps, box_n_field=n)
+    return cfg
+
+
+def initial_field(cfg: HMMConfig, seed: Optional[int] = None) -> np.ndarray:
+    """Seeded macro initial data M0 (3, P) for a named configuration."""
+    if cfg.dim == 1:
+        x = macro_coords(cfg)[0]
+        m = c1_initial(x)
+    else:
+        base = 20210820
+        s = base + (CONFIG_NAMES.index(cfg.name) if cfg.name in CONFIG_NAMES else 7)
+        m = fourier_field(cfg, s if seed is None else seed)
+    return np.ascontiguousarray(m.reshape(3, -1))
