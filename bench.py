@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the HMM micro-problem path on GB300.
+
+A step is one full HMM macro step (MPEA, Section 3.1) of the field model on the
+2D workload: a 128^2 periodic macro grid, one 64^2-node micro box per macro
+point (16384 micro problems), 400 HeunP micro steps each, eps = 1/200,
+a = 1 + 0.5 sin(2 pi y1) sin(2 pi y2), alpha = 0.05, alpha_micro = 1.2,
+4th-order stencil. The headline value is micro lattice updates per second of
+the batched FP32 form; the plain FP64 method is timed on the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: each rank runs an independent replica (the micro problems of one
+macro grid are independent; no collective on the data path), the value is
+the total over ranks divided by the slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "micro lattice updates/s + HMM macro steps/s, FP32-batched vs FP64, <=1e-6 rel err"
+UNIT = "LU/s"
+WORKLOAD = "c2_2d"
+WORKLOAD_DESC = ("2D HMM, 128^2 periodic macro grid, 16384 micro boxes of 64^2 nodes "
+                 "(8 per eps, eps=1/200), 400 HeunP micro steps, 4th-order stencil, "
+                 "a=1+0.5sin(2pi y1)sin(2pi y2), alpha=0.05, alpha_micro=1.2")
+FLOPS_PER_LU_2D = 232.0     # algorithmic FP32 flops per lattice update
+BYTES_PER_LU_FP32 = 24.0    # streaming-model bytes per lattice update
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def _oracle_chunk(args):
+    name, points = args
+    import workloads as W
+    from oracle import hmm_oracle as O
+    cfg = W.config(name)
+    M0 = W.initial_field(cfg)
+    t = time.perf_counter()
+    O.micro_batch(cfg, M0, points=points)
+    return time.perf_counter() - t
+
+
+def oracle_sample(name: str, boxes_per_worker: int, workers: int, pool=None):
+    """Time the oracle on a bounded sample of boxes of the workload; returns (LU/s, info)."""
+    import workloads as W
+    from oracle import hmm_oracle as O
+    cfg = W.config(name)
+    n = workers * boxes_per_worker
+    stride = max(1, cfg.n_points // n)
+    pts = [i * stride for i in range(n)]
+    chunks = [(name, pts[w * boxes_per_worker:(w + 1) * boxes_per_worker]) for w in range(workers)]
+    t0 = time.perf_counter()
+    if pool is None:
+        for c in chunks:
+            _oracle_chunk(c)
+    else:
+        pool.map(_oracle_chunk, chunks)
+    wall = time.perf_counter() - t0
+    lu = 0.0
+    for p in pts:
+        g = O.box_geometry(cfg, p)
+        lu += (g["N"] - 2 * g["r"]) ** cfg.dim * g["M"]
+    return lu / wall, dict(boxes=n, wall_s=wall, lu=lu)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2108_09463_gb300 import HMM, build
+
+    # Spawned CPU workers for the oracle baseline start before any GPU work.
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(args.cpu_workers)
+
+    build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = W.config(WORKLOAD)
+    M0 = W.initial_field(cfg)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def timed_steps(fn, k):
+        """k calls of fn, each bracketed by CUDA events on the current stream, L2 flushed between."""
+        tot = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    # --- FP32 batched form: full macro steps (RK4P start-up inside warm-up, then MPEA).
+    h32 = HMM(cfg, precision=1)
+    lu_batch, _ = h32.stats()
+    M = torch.from_numpy(M0).cuda()
+    for _ in range(args.warmup):
+        h32.macro_step(M, 1)
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        ms32 = timed_steps(lambda: h32.macro_step(M, 1), args.steps)
+    barrier()
+    t_local = torch.tensor([ms32], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * args.steps * lu_batch / (ms_max / 1e3)
+    macro_steps_per_s = args.steps / (ms_max / 1e3)
+
+    # --- dominant kernel: the FP32 micro-batch kernel, timed per launch on its stream.
+    H = torch.empty_like(M)
+    kms = []
+    for _ in range(args.kernel_reps):
+        flush.zero_()
+        h32.micro_batch(M, H)
+        kms.append(h32.stats()[1])
+    k_ms = sum(kms) / len(kms)
+    flops = FLOPS_PER_LU_2D * lu_batch
+    peaks = _peaks()
+    clocks = clk.summary()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    props = torch.cuda.get_device_properties(local_rank)
+    n_sm = props.multi_processor_count
+    alu_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (k_ms / 1e3) / 1e12
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": args.traffic,
+                "kernel": "micro_fp32_kernel<2,3>", "kernel_ms": k_ms,
+                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
+                "hbm_streaming_equivalent": {
+                    "GB_per_s": BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9,
+                    "frac_of_measured_hbm": BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9 / hbm}}
+
+    # --- accuracy of the FP32 form against the FP64 GPU method on the same macro state.
+    h64 = HMM(cfg, precision=0)
+    Mfix = torch.from_numpy(M0).cuda()
+    H32 = h32.micro_batch(Mfix).cpu().numpy()
+    H64 = h64.micro_batch(Mfix).cpu().numpy()
+    rel = float(np.linalg.norm(H32 - H64, axis=0).max() / np.linalg.norm(H64, axis=0).max())
+
+    # --- plain FP64 method: MPEA steps on the same workload (history set so j >= 2).
+    hist = torch.zeros((2, 3, cfg.n_points), dtype=torch.float64, device="cuda")
+    h64.set_state(hist, 2)
+    M64 = torch.from_numpy(M0).cuda()
+    h64.macro_step(M64, 1)
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    ms64 = timed_steps(lambda: h64.macro_step(M64, 1), k64)
+    lu64 = k64 * lu_batch / (ms64 / 1e3)
+    h64.close()
+
+    # --- end to end through the C ABI with host buffers (copies inside the timed region).
+    Mh = torch.from_numpy(M0).pin_memory().numpy()
+    he = HMM(cfg, precision=1)
+    he.macro_step_host(Mh, 3)           # start-up steps + graph capture outside the timing
+    ke = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        he.macro_step_host(Mh, 1)
+    e2e_s = time.perf_counter() - t0
+    he.close()
+    e2e = {"value": world * ke * lu_batch / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * cfg.n_points * 8, "d2h_bytes_per_step": 3 * cfg.n_points * 8,
+           "macro_steps_per_s": ke / e2e_s}
+
+    cpu = None
+    if pool is not None:
+        oracle_sample(WORKLOAD, 1, args.cpu_workers, pool)   # warm the workers (imports)
+        v, info = oracle_sample(WORKLOAD, args.cpu_boxes_per_worker, args.cpu_workers, pool)
+        pool.close()
+        cpu = {"value": v, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
+               "sample": f"{info['boxes']} of the 16384 micro boxes (full 64^2 x 400 steps each), "
+                         f"{args.cpu_workers} spawned processes, {info['wall_s']:.1f} s wall"}
+    h32.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "boxes": cfg.n_points, "micro_nodes": 64,
+                       "micro_steps": 400, "lu_per_step": lu_batch, "precision": "fp32-batched",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "macro_steps_per_s": macro_steps_per_s,
+            "fp64_plain": {"value": lu64, "unit": UNIT, "macro_steps_per_s": k64 / (ms64 / 1e3),
+                           "steps": k64},
+            "speedup_fp32_vs_fp64": value / world / lu64,
+            "fp32_vs_fp64_rel_err": rel,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 3 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    workers = args.cpu_workers
+    pool = mp.get_context("spawn").Pool(workers)
+    oracle_sample(WORKLOAD, 1, workers, pool)
+    for _ in range(args.warmup):
+        oracle_sample(WORKLOAD, args.ref_boxes_per_worker, workers, pool)
+    tot_lu, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        v, info = oracle_sample(WORKLOAD, args.ref_boxes_per_worker, workers, pool)
+        tot_lu += info["lu"]
+        tot_s += info["wall_s"]
+    pool.close()
+    value = tot_lu / tot_s
+    sample = (f"each step: {workers * args.ref_boxes_per_worker} of the 16384 micro boxes "
+              f"(full 64^2 x 400 steps), {workers} spawned processes")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--kernel-reps", type=int, default=3)
+    ap.add_argument("--cpu-workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--cpu-boxes-per-worker", type=int, default=16)
+    ap.add_argument("--ref-boxes-per-worker", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * hmm.h -- C ABI of the GB300 library for the heterogeneous multiscale method
+ * (HMM) for the Landau-Lifshitz equation with an oscillatory exchange
+ * coefficient a^eps (Leitenmaier & Runborg, "Heterogeneous multiscale methods
+ * for the Landau-Lifshitz equation").
+ *
+ * The problem (Section 2.1, eq. prob): on the periodic domain [0, L]^d find M
+ * with dM/dt = -M x H - alpha M x (M x H), H = div(a^eps grad M), |M| = 1.
+ * HMM (Section 2.2) evolves a coarse macro grid x_i = i*DX with the field model
+ * (eq. macro_disc) dM_i/dt = -M_i x H_avg,i - alpha M_i x (M_i x H_avg,i), where
+ * H_avg,i comes from a micro problem around x_i (eq. micro) averaged by the
+ * kernel-weighted space-time average (Section 2.3, eq. upscaling).
+ *
+ * Conventions shared by every call:
+ *  - A macro field is P = n_macro[0]*...*n_macro[d-1] points, FP64, stored SoA:
+ *    component c of point p at [c*P + p]; p is the C-order linear index of the
+ *    multi-index (i_1, ..., i_d) with i_d fastest. Both precision modes keep the
+ *    macro fields in FP64; only the micro state of HMM_FP32_BATCHED is FP32.
+ *  - "_dev" pointers are device pointers on the device that was current at
+ *    hmm_init; "_host" pointers are ordinary host memory (pinned or pageable).
+ *    The caller owns every buffer it passes; the library never frees or
+ *    retains them beyond the call (except host arrays inside hmm_params, which
+ *    hmm_init copies).
+ *  - All work is enqueued on the stream given to hmm_init, and every call that
+ *    returns a result synchronises that stream before returning.
+ *  - No call throws. Every call returns an hmm_status; hmm_last_error() gives
+ *    a one-line reason for the last failure on a handle.
+ *  - A handle is not thread safe: calls on one handle must not overlap.
+ */
+#ifndef HMM_GB300_H
+#define HMM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMM_OK = 0,
+  HMM_ERR_INVALID_ARG = 1,     /* a parameter or pointer is out of its domain   */
+  HMM_ERR_UNSTABLE_DT = 2,     /* a given time step exceeds the stability bound */
+  HMM_ERR_OUT_OF_MEMORY = 3,   /* a device allocation failed                    */
+  HMM_ERR_CUDA = 4,            /* a CUDA runtime call failed                    */
+  HMM_ERR_TIMEOUT = 5,         /* reserved: the kernels contain no spin waits   */
+  HMM_ERR_NONFINITE = 6,       /* a non-finite value or |m| blow-up on device   */
+  HMM_ERR_NOT_INITIALISED = 7  /* null or destroyed handle                      */
+} hmm_status;
+
+typedef enum {
+  HMM_FP64_PLAIN = 0,    /* micro state and arithmetic in FP64                */
+  HMM_FP32_BATCHED = 1   /* FP32 perturbation-form micro state, FP64 averages */
+} hmm_precision;
+
+/* One term of the material coefficient (Section 2.1 (A1); the examples of
+ * Section 2.4 and Section 5 are sums of such terms):
+ *     amp * prod_{k<d} g_k(2*pi*omega[k]*s_k + phase[k]),
+ * g_k = 1 (kind 0), sin (kind 1) or cos (kind 2); s_k = x_k/eps (scale 0, the
+ * fast variable) or s_k = x_k (scale 1, the slow variable). */
+typedef struct {
+  double amp;
+  int kind[3];
+  int scale[3];
+  double omega[3];
+  double phase[3];
+} hmm_coef_term;
+
+/* Parameters of one HMM problem (copied by hmm_init). Section references:
+ * damping alpha (A2) and the artificial micro damping alpha_micro (Section 2.3,
+ * end; Section 4.3); box half-width mu' and averaging half-width mu (eq.
+ * upscaling, Section 4.3); micro grid dx = eps/pts_per_eps (Section 4.4);
+ * kernel parameters p, q (Definition of K^{p,q}); interpolation order 2k
+ * (Section 4.1, eq. Q_k). */
+typedef struct {
+  int dim;                      /* d = 1, 2 or 3                                   */
+  int n_macro[3];               /* macro points per axis (entries >= dim ignored)  */
+  double L;                     /* domain length; DX = L/n_macro[k]                */
+  double alpha;                 /* macro damping, 0 < alpha <= 1 (A2)              */
+  double alpha_micro;           /* micro damping, 0 < alpha_micro <= 4             */
+  double dt_macro;              /* macro step; <= 0: 0.06*DX^2/(d*a_max)          */
+  double c0;                    /* a(x) = c0 + sum of terms                        */
+  int n_terms;                  /* 0..8                                            */
+  const hmm_coef_term* terms;   /* host array of n_terms terms                     */
+  double eps;                   /* uniform eps (used when eps_field is NULL)       */
+  const double* eps_field;      /* host array of P eps_i values, or NULL           */
+  int box_n;                    /* micro nodes per axis N, ring included           */
+  const int* box_n_field;       /* host array of P values N_i, or NULL             */
+  double pts_per_eps;           /* K: micro grid spacing dx = eps_i/K              */
+  double mu_over_eps;           /* mu/eps; <= 0: mu = 0.8*mu', mu' = (N-1)dx/2     */
+  int micro_steps;              /* M micro time steps (eta = M*dt_micro)           */
+  double dt_safety;             /* dt_micro as a fraction of the HeunP stability
+                                   limit (eq. Cstab); <= 0: 0.8                    */
+  int px, qx, pt, qt;           /* kernel parameters; <= 0: 3, 7, 3, 7             */
+  int interp_order;             /* 2k in {2, 4}; <= 0: 4                           */
+  int stencil_order;            /* 2 or 4; <= 0: 4                                 */
+  int precision;                /* hmm_precision                                   */
+  int kernel_variant;           /* HMM_FP32_BATCHED: 0 or 1 generic arena kernel,
+                                   2 resident 2D kernel (d = 2, N - 2r <= 64)       */
+  int reserved[4];              /* must be zero                                    */
+} hmm_params;
+
+/* Set-up (host only, plus device allocations on the current device).
+ * Validates the parameters: 0 < alpha <= 1, 0 < alpha_micro <= 4, eps > 0,
+ * n_macro >= 2k+1 per axis, 2r+2 <= N <= 1024/256/64 for d = 1/2/3, a > 0 at
+ * every micro face (checked on the device during each micro batch), and that
+ * the averaging box [-mu, mu]^d stays inside the interior (off the Dirichlet
+ * ring of width r = 1 or 3). Computes the smoothing kernels, the quadrature
+ * weight tables, the micro time step of each box (dt = dt_safety *
+ * s_max(alpha_micro) dx^2 / (a_max d lambda_s)), sorts the boxes by cost
+ * (longest first) and allocates the per-CTA arenas.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * On success *handle_out owns all library memory until hmm_destroy. */
+hmm_status hmm_init(const hmm_params* params, void* cuda_stream, void** handle_out);
+
+/* The batched micro-problem solve (the hot path): for every macro point x_i,
+ * build m_init = Q_[2k](x_i + xi) from M (Section 4.1), time-step the micro
+ * problem (eq. micro) with HeunP on [-mu', mu']^d with m - m_init = 0 on the
+ * ring (Section 4.2), and reduce H = div(a^eps grad m) by the kernel-weighted
+ * average (eq. upscaling) into H_avg,i. M_dev and Havg_dev: SoA 3 x P FP64
+ * device buffers; Havg_dev is overwritten. Pure: the macro history is not
+ * touched. Returns HMM_ERR_NONFINITE if a micro state blew up. */
+hmm_status hmm_micro_batch(void* handle, const double* M_dev, double* Havg_dev);
+
+/* As hmm_micro_batch, with host buffers: copies M_host to the device, runs the
+ * batch and copies H_avg back, all on the handle's stream. */
+hmm_status hmm_micro_batch_host(void* handle, const double* M_host, double* Havg_host);
+
+/* n_steps macro steps of the field model (eq. macro_disc), in place on M_dev
+ * (SoA 3 x P FP64). Steps j = 0 and 1 use RK4P (Section 3.1) with one micro
+ * batch per stage at the normalised stage state; later steps use MPEA
+ * (eqs. h_term, h_mpea, mpe_update), one micro batch per step. MPEA steps are
+ * replayed from a CUDA graph captured on first use for this M_dev. */
+hmm_status hmm_macro_step(void* handle, double* M_dev, int n_steps);
+
+/* As hmm_macro_step with M in host memory (copied in and out once per call). */
+hmm_status hmm_macro_step_host(void* handle, double* M_host, int n_steps);
+
+/* Restart state of the macro stepper: the MPEA history hist (2 x 3 x P FP64
+ * device buffer: h^{j-1} then h^{j-2}, eq. h_term) and the step count j. The
+ * macro field itself is the caller's M. get copies out, set copies in. */
+hmm_status hmm_get_state(void* handle, double* hist_dev, long long* j);
+hmm_status hmm_set_state(void* handle, const double* hist_dev, long long j);
+
+/* Lattice updates (micro nodes x micro steps, interior nodes only) of one
+ * micro batch, and the device time of the last micro batch in ms. */
+hmm_status hmm_stats(void* handle, double* lattice_updates_per_batch, double* last_batch_ms);
+
+/* Per-box quantities as the library computed them, host arrays of length P in
+ * macro-point order: dt_micro, mu, dx and N. Any pointer may be NULL. */
+hmm_status hmm_box_info(void* handle, double* dt, double* mu, double* dx, int* n);
+
+/* The macro time step the handle uses. */
+hmm_status hmm_macro_dt(void* handle, double* dt_macro);
+
+/* One-line description of the last failure on this handle ("" if none). Valid
+ * until the next call on the handle. NULL handle: the last hmm_init failure. */
+const char* hmm_last_error(void* handle);
+
+/* Frees all library memory of the handle (synchronises its stream). */
+void hmm_destroy(void* handle);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMM_GB300_H */

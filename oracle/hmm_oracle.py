@@ -98,10 +98,19 @@ def _solve_fractions(A: List[List[Fraction]], b: List[Fraction]) -> List[Fractio
     return [M[i][n] / M[i][i] for i in range(n)]
 
 
-def kernel_eval(x, p: int = 3, q: int = 7) -> np.ndarray:
+def _as(v: Fraction, dtype):
+    """A rational in the working precision (numerator and denominator rounded once each)."""
+    return dtype(v.numerator) / dtype(v.denominator)
+
+
+def _pi(dtype):
+    return dtype(np.pi) if np.dtype(dtype) == np.float64 else 4 * np.arctan(dtype(1))
+
+
+def kernel_eval(x, p: int = 3, q: int = 7, dtype=np.float64) -> np.ndarray:
     """K(x) in K^{p,q}, zero outside (-1, 1)."""
-    c = [float(v) for v in kernel_coefficients(p, q)]
-    x = np.asarray(x, dtype=np.float64)
+    c = [_as(v, dtype) for v in kernel_coefficients(p, q)]
+    x = np.asarray(x, dtype=dtype)
     poly = np.zeros_like(x)
     for k in reversed(range(len(c))):
         poly = poly * x + c[k]
@@ -109,10 +118,10 @@ def kernel_eval(x, p: int = 3, q: int = 7) -> np.ndarray:
     return np.where(inside, (1.0 - x * x) ** (q + 1) * poly, 0.0)
 
 
-def kernel0_eval(t, p: int = 3, q: int = 7) -> np.ndarray:
+def kernel0_eval(t, p: int = 3, q: int = 7, dtype=np.float64) -> np.ndarray:
     """K0(t) in K0^{p,q}, zero outside (0, 1)."""
-    c = [float(v) for v in kernel0_coefficients(p, q)]
-    t = np.asarray(t, dtype=np.float64)
+    c = [_as(v, dtype) for v in kernel0_coefficients(p, q)]
+    t = np.asarray(t, dtype=dtype)
     poly = np.zeros_like(t)
     for k in reversed(range(len(c))):
         poly = poly * t + c[k]
@@ -120,24 +129,24 @@ def kernel0_eval(t, p: int = 3, q: int = 7) -> np.ndarray:
     return np.where(inside, (t * (1.0 - t)) ** (q + 1) * poly, 0.0)
 
 
-def space_weights(N: int, dx: float, mu: float, p: int, q: int) -> np.ndarray:
+def space_weights(N: int, dx: float, mu: float, p: int, q: int, dtype=np.float64) -> np.ndarray:
     """Discrete 1D weights of K_mu at the micro nodes xi_j (eq. upscaling).
 
     Trapezoid rule: W_j proportional to dx*K_mu(xi_j) = (dx/mu) K(xi_j/mu), then
     normalised to sum exactly 1 (reading G2). xi_j = (j - (N-1)/2) dx (reading G6).
     """
-    xi = (np.arange(N) - (N - 1) / 2.0) * dx
-    W = kernel_eval(xi / mu, p, q)
+    xi = (np.arange(N, dtype=dtype) - dtype(N - 1) / 2) * dtype(dx)
+    W = kernel_eval(xi / dtype(mu), p, q, dtype)
     return W / W.sum()
 
 
-def time_weights(M: int, p: int, q: int) -> np.ndarray:
+def time_weights(M: int, p: int, q: int, dtype=np.float64) -> np.ndarray:
     """Discrete weights w_n, n = 0..M, of K0_eta at t_n = n*dt, eta = M*dt.
 
     Trapezoid rule, normalised to sum exactly 1 (reading G2). w_0 = w_M = 0.
     """
-    t = np.arange(M + 1) / M
-    w = kernel0_eval(t, p, q)
+    t = np.arange(M + 1, dtype=dtype) / dtype(M)
+    w = kernel0_eval(t, p, q, dtype)
     return w / w.sum()
 
 
@@ -230,9 +239,9 @@ def box_geometry(cfg, p: int) -> Dict:
                 mu_prime=mup, mu=mu, r=r, dt=micro_dt(cfg, dx), M=int(cfg.micro_steps))
 
 
-def node_offsets(N: int, dx: float) -> np.ndarray:
+def node_offsets(N: int, dx: float, dtype=np.float64) -> np.ndarray:
     """Micro node coordinates xi_j = (j - (N-1)/2) dx, j = 0..N-1 (reading G6)."""
-    return (np.arange(N) - (N - 1) / 2.0) * dx
+    return (np.arange(N, dtype=dtype) - dtype(N - 1) / 2) * dtype(dx)
 
 
 # --------------------------------------------------------------------------
@@ -242,9 +251,11 @@ def node_offsets(N: int, dx: float) -> np.ndarray:
 
 def lagrange_basis(s: np.ndarray, k: int) -> np.ndarray:
     """Lagrange basis l_a(s), a = -k..k, on the integer nodes -k..k; shape (len(s), 2k+1)."""
-    s = np.asarray(s, dtype=np.float64)
+    s = np.asarray(s)
+    if s.dtype.kind != "f":
+        s = s.astype(np.float64)
     nodes = np.arange(-k, k + 1)
-    out = np.ones((s.size, nodes.size))
+    out = np.ones((s.size, nodes.size), dtype=s.dtype)
     for ia, a in enumerate(nodes):
         for b in nodes:
             if b != a:
@@ -275,12 +286,12 @@ def interpolate_P(neigh: np.ndarray, s_axes: Sequence[np.ndarray], k: int) -> np
     return P
 
 
-def micro_initial(cfg, M: np.ndarray, geo: Dict, normalise: bool = True) -> np.ndarray:
+def micro_initial(cfg, M: np.ndarray, geo: Dict, normalise: bool = True, dtype=np.float64) -> np.ndarray:
     """m_init = Q_[2k](x_i + xi) = P/|P| on all micro nodes (eq. Q_k)."""
     k = cfg.interp_order // 2
-    neigh = gather_neighbourhood(cfg, M, geo["idx"])
-    xi = node_offsets(geo["N"], geo["dx"])
-    s_axes = [xi / geo["DX"][a] for a in range(cfg.dim)]
+    neigh = gather_neighbourhood(cfg, M, geo["idx"]).astype(dtype)
+    xi = node_offsets(geo["N"], geo["dx"], dtype)
+    s_axes = [xi / dtype(geo["DX"][a]) for a in range(cfg.dim)]
     P = interpolate_P(neigh, s_axes, k)
     if not normalise:
         return P
@@ -292,22 +303,23 @@ def micro_initial(cfg, M: np.ndarray, geo: Dict, normalise: bool = True) -> np.n
 # --------------------------------------------------------------------------
 
 
-def coef_eval(cfg, eps: float, X: Sequence[np.ndarray]) -> np.ndarray:
+def coef_eval(cfg, eps: float, X: Sequence[np.ndarray], dtype=np.float64) -> np.ndarray:
     """a(x) = c0 + sum_t amp_t prod_k g_tk(2 pi omega_tk s_k + phase_tk), s = x/eps or x."""
-    out = np.full(np.broadcast(*X).shape, float(cfg.c0))
+    out = np.full(np.broadcast(*X).shape, dtype(cfg.c0), dtype=dtype)
+    two_pi = 2 * _pi(dtype)
     for t in cfg.terms:
-        val = np.full_like(out, float(t.amp))
+        val = np.full_like(out, dtype(t.amp))
         for k in range(cfg.dim):
             if t.kind[k] == 0:
                 continue
-            s = X[k] / eps if t.scale[k] == 0 else X[k]
-            th = 2.0 * math.pi * t.omega[k] * s + t.phase[k]
+            s = X[k] / dtype(eps) if t.scale[k] == 0 else X[k]
+            th = two_pi * dtype(t.omega[k]) * s + dtype(t.phase[k])
             val = val * (np.sin(th) if t.kind[k] == 1 else np.cos(th))
         out = out + val
     return out
 
 
-def face_coefficients(cfg, geo: Dict) -> List[np.ndarray]:
+def face_coefficients(cfg, geo: Dict, dtype=np.float64) -> List[np.ndarray]:
     """a^eps at the faces of each axis: for axis k, shape (N,..,N-1 at axis k,..,N).
 
     Face j+1/2 along axis k lies at xi_k = (j + 1/2 - (N-1)/2) dx, the other
@@ -315,8 +327,8 @@ def face_coefficients(cfg, geo: Dict) -> List[np.ndarray]:
     coordinate x_i + xi (fast variable with the box's eps).
     """
     d, N, dx = cfg.dim, geo["N"], geo["dx"]
-    xi = node_offsets(N, dx)
-    xf = (np.arange(N - 1) + 0.5 - (N - 1) / 2.0) * dx
+    xi = node_offsets(N, dx, dtype)
+    xf = (np.arange(N - 1, dtype=dtype) + dtype(0.5) - dtype(N - 1) / 2) * dtype(dx)
     out = []
     for k in range(d):
         X = []
@@ -324,8 +336,8 @@ def face_coefficients(cfg, geo: Dict) -> List[np.ndarray]:
             v = xf if a == k else xi
             shp = [1] * d
             shp[a] = v.size
-            X.append(geo["xc"][a] + v.reshape(shp))
-        out.append(coef_eval(cfg, geo["eps"], X))
+            X.append(dtype(geo["xc"][a]) + v.reshape(shp))
+        out.append(coef_eval(cfg, geo["eps"], X, dtype))
     return out
 
 
@@ -446,7 +458,7 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
     cax = m_init.ndim - d - 1
     m = m_init.copy()
     inner = _interior(m, d, r)
-    S = np.zeros(m.shape[:cax] + (3,))
+    S = np.zeros(m.shape[:cax] + (3,), dtype=m.dtype)
     Wb = W[(None,) * (cax + 1)]
     red = tuple(range(cax + 1, m.ndim))
     energies, normdev = [], []
@@ -477,31 +489,36 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
 
 
 def micro_batch(cfg, M: np.ndarray, points: Optional[Sequence[int]] = None,
-                group: int = 64) -> np.ndarray:
-    """H_avg(x_i; M) for macro points ``points`` (default all); returns (3, len)."""
+                group: int = 64, dtype=np.float64) -> np.ndarray:
+    """H_avg(x_i; M) for macro points ``points`` (default all); returns (3, len).
+
+    ``dtype`` is the working precision (FP64 by default; np.longdouble gives a
+    reference with a lower rounding floor, used to bound the FP64 results' own
+    rounding error).
+    """
     P = cfg.n_points
     pts = list(range(P)) if points is None else [int(p) for p in points]
-    out = np.zeros((3, len(pts)))
+    out = np.zeros((3, len(pts)), dtype=dtype)
     geos = [box_geometry(cfg, p) for p in pts]
     keys: Dict[Tuple, List[int]] = {}
     for i, g in enumerate(geos):
         keys.setdefault((g["N"], g["dx"], g["dt"], g["mu"]), []).append(i)
     for (N, dx, dt, mu), members in keys.items():
         d, r = cfg.dim, geos[members[0]]["r"]
-        Wfull = space_weights(N, dx, mu, cfg.px, cfg.qx)
+        Wfull = space_weights(N, dx, mu, cfg.px, cfg.qx, dtype)
         if np.any(Wfull[:r] != 0.0) or np.any(Wfull[N - r:] != 0.0):
             raise ValueError("averaging box [-mu, mu] reaches the Dirichlet ring")
         W1 = Wfull[r:N - r]
         W = W1
         for _ in range(d - 1):
             W = np.multiply.outer(W, W1)
-        w = time_weights(cfg.micro_steps, cfg.pt, cfg.qt)
+        w = time_weights(cfg.micro_steps, cfg.pt, cfg.qt, dtype)
         for s in range(0, len(members), group):
             chunk = members[s:s + group]
-            mi = np.stack([micro_initial(cfg, M, geos[i]) for i in chunk])
-            af = [np.stack([face_coefficients(cfg, geos[i])[k] for i in chunk]) for k in range(d)]
-            S = micro_solve(mi, af, dx, dt, cfg.micro_steps, cfg.alpha_micro, W, w,
-                            cfg.stencil_order)
+            mi = np.stack([micro_initial(cfg, M, geos[i], dtype=dtype) for i in chunk])
+            af = [np.stack([face_coefficients(cfg, geos[i], dtype)[k] for i in chunk]) for k in range(d)]
+            S = micro_solve(mi, af, dtype(dx), dtype(dt), cfg.micro_steps, dtype(cfg.alpha_micro),
+                            W, w, cfg.stencil_order)
             for j, i in enumerate(chunk):
                 out[:, i] = S[j]
     return out

@@ -1,0 +1,225 @@
+"""ctypes binding of the C ABI in include/hmm.h (argument marshalling only).
+
+Every step of the HMM path runs in the library's CUDA kernels; this module
+only converts Python/torch arguments into the C structs and pointers. There is
+no fallback: if libhmm_gb300.so is missing or fails to load, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhmm_gb300.so")
+
+HMM_OK = 0
+STATUS_NAMES = {0: "HMM_OK", 1: "HMM_ERR_INVALID_ARG", 2: "HMM_ERR_UNSTABLE_DT",
+                3: "HMM_ERR_OUT_OF_MEMORY", 4: "HMM_ERR_CUDA", 5: "HMM_ERR_TIMEOUT",
+                6: "HMM_ERR_NONFINITE", 7: "HMM_ERR_NOT_INITIALISED"}
+HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
+
+# The symbols include/hmm.h declares (checked by the CPU test suite).
+EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
+            "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
+            "hmm_box_info", "hmm_macro_dt", "hmm_last_error", "hmm_destroy")
+
+
+class HmmCoefTerm(ctypes.Structure):
+    _fields_ = [("amp", c_double), ("kind", c_int * 3), ("scale", c_int * 3),
+                ("omega", c_double * 3), ("phase", c_double * 3)]
+
+
+class HmmParams(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n_macro", c_int * 3), ("L", c_double), ("alpha", c_double),
+                ("alpha_micro", c_double), ("dt_macro", c_double), ("c0", c_double),
+                ("n_terms", c_int), ("terms", POINTER(HmmCoefTerm)), ("eps", c_double),
+                ("eps_field", POINTER(c_double)), ("box_n", c_int), ("box_n_field", POINTER(c_int)),
+                ("pts_per_eps", c_double), ("mu_over_eps", c_double), ("micro_steps", c_int),
+                ("dt_safety", c_double), ("px", c_int), ("qx", c_int), ("pt", c_int), ("qt", c_int),
+                ("interp_order", c_int), ("stencil_order", c_int), ("precision", c_int),
+                ("kernel_variant", c_int), ("reserved", c_int * 4)]
+
+
+class HmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhmm_gb300.so and declare the signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run paper_2108_09463_gb300.build.build() "
+                          "(the HMM path has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    lib.hmm_init.argtypes = [POINTER(HmmParams), c_void_p, POINTER(c_void_p)]
+    lib.hmm_micro_batch.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.hmm_micro_batch_host.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.hmm_macro_step.argtypes = [c_void_p, c_void_p, c_int]
+    lib.hmm_macro_step_host.argtypes = [c_void_p, c_void_p, c_int]
+    lib.hmm_get_state.argtypes = [c_void_p, c_void_p, POINTER(c_longlong)]
+    lib.hmm_set_state.argtypes = [c_void_p, c_void_p, c_longlong]
+    lib.hmm_stats.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
+    lib.hmm_box_info.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.hmm_macro_dt.argtypes = [c_void_p, POINTER(c_double)]
+    lib.hmm_last_error.argtypes = [c_void_p]
+    lib.hmm_last_error.restype = c_char_p
+    lib.hmm_destroy.argtypes = [c_void_p]
+    lib.hmm_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("hmm_last_error", "hmm_destroy"):
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def make_params(cfg, precision=None, kernel_variant=0):
+    """Fill HmmParams from a problem description (an object with HMMConfig's fields).
+
+    Returns (params, keepalive): keepalive holds the arrays params points to.
+    """
+    import numpy as np
+    terms = (HmmCoefTerm * max(1, len(cfg.terms)))()
+    for i, t in enumerate(cfg.terms):
+        terms[i].amp = float(t.amp)
+        for k in range(3):
+            terms[i].kind[k] = int(t.kind[k]) if k < cfg.dim else 0
+            terms[i].scale[k] = int(t.scale[k])
+            terms[i].omega[k] = float(t.omega[k])
+            terms[i].phase[k] = float(t.phase[k])
+    p = HmmParams()
+    p.dim = int(cfg.dim)
+    for k in range(3):
+        p.n_macro[k] = int(list(cfg.n_macro)[k]) if k < len(cfg.n_macro) else 1
+    p.L = float(cfg.L)
+    p.alpha = float(cfg.alpha)
+    p.alpha_micro = float(cfg.alpha_micro)
+    p.dt_macro = float(cfg.dt_macro)
+    p.c0 = float(cfg.c0)
+    p.n_terms = len(cfg.terms)
+    p.terms = ctypes.cast(terms, POINTER(HmmCoefTerm))
+    p.eps = float(cfg.eps)
+    keep = [terms]
+    if cfg.eps_field is not None:
+        ef = np.ascontiguousarray(cfg.eps_field, dtype=np.float64)
+        keep.append(ef)
+        p.eps_field = ef.ctypes.data_as(POINTER(c_double))
+    p.box_n = int(cfg.box_n)
+    if cfg.box_n_field is not None:
+        nf = np.ascontiguousarray(cfg.box_n_field, dtype=np.int32)
+        keep.append(nf)
+        p.box_n_field = nf.ctypes.data_as(POINTER(c_int))
+    p.pts_per_eps = float(cfg.pts_per_eps)
+    p.mu_over_eps = float(cfg.mu_over_eps)
+    p.micro_steps = int(cfg.micro_steps)
+    p.dt_safety = float(cfg.dt_safety)
+    p.px, p.qx, p.pt, p.qt = int(cfg.px), int(cfg.qx), int(cfg.pt), int(cfg.qt)
+    p.interp_order = int(cfg.interp_order)
+    p.stencil_order = int(cfg.stencil_order)
+    p.precision = int(cfg.precision if precision is None else precision)
+    p.kernel_variant = int(kernel_variant)
+    return p, keep
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if hasattr(t, "data_ptr") else t.ctypes.data
+
+
+class HMM:
+    """One HMM problem on the current CUDA device (a handle of the C ABI)."""
+
+    def __init__(self, cfg, precision=None, stream=None, kernel_variant=0):
+        import torch
+        self.lib = load_library()
+        self.cfg = cfg
+        self.P = int(cfg.n_points)
+        params, keep = make_params(cfg, precision, kernel_variant)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = c_void_p()
+        st = self.lib.hmm_init(ctypes.byref(params), c_void_p(stream.cuda_stream), ctypes.byref(h))
+        del keep
+        if st != HMM_OK:
+            raise HmmError(st, self.lib.hmm_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != HMM_OK:
+            raise HmmError(st, self.lib.hmm_last_error(self.h).decode())
+
+    def _field(self, M):
+        import torch
+        if not (isinstance(M, torch.Tensor) and M.is_cuda and M.dtype == torch.float64
+                and M.is_contiguous() and tuple(M.shape) == (3, self.P)):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of shape (3, {self.P})")
+        return M
+
+    def micro_batch(self, M, out=None):
+        import torch
+        M = self._field(M)
+        if out is None:
+            out = torch.empty_like(M)
+        self._check(self.lib.hmm_micro_batch(self.h, c_void_p(M.data_ptr()), c_void_p(self._field(out).data_ptr())))
+        return out
+
+    def micro_batch_host(self, M, out):
+        """M, out: contiguous float64 host arrays/tensors of shape (3, P)."""
+        self._check(self.lib.hmm_micro_batch_host(self.h, c_void_p(_ptr(M)), c_void_p(_ptr(out))))
+        return out
+
+    def macro_step(self, M, n_steps=1):
+        M = self._field(M)
+        self._check(self.lib.hmm_macro_step(self.h, c_void_p(M.data_ptr()), int(n_steps)))
+        return M
+
+    def macro_step_host(self, M, n_steps=1):
+        self._check(self.lib.hmm_macro_step_host(self.h, c_void_p(_ptr(M)), int(n_steps)))
+        return M
+
+    def get_state(self):
+        import torch
+        hist = torch.empty((2, 3, self.P), dtype=torch.float64, device="cuda")
+        j = c_longlong()
+        self._check(self.lib.hmm_get_state(self.h, c_void_p(hist.data_ptr()), ctypes.byref(j)))
+        return hist, int(j.value)
+
+    def set_state(self, hist, j):
+        ptr = c_void_p(hist.data_ptr()) if hist is not None else c_void_p()
+        self._check(self.lib.hmm_set_state(self.h, ptr, int(j)))
+
+    def stats(self):
+        lu, ms = c_double(), c_double()
+        self._check(self.lib.hmm_stats(self.h, ctypes.byref(lu), ctypes.byref(ms)))
+        return lu.value, ms.value
+
+    def box_info(self):
+        import numpy as np
+        dt, mu, dx = (np.empty(self.P) for _ in range(3))
+        n = np.empty(self.P, dtype=np.int32)
+        self._check(self.lib.hmm_box_info(self.h, c_void_p(dt.ctypes.data), c_void_p(mu.ctypes.data),
+                                          c_void_p(dx.ctypes.data), c_void_p(n.ctypes.data)))
+        return dict(dt=dt, mu=mu, dx=dx, N=n)
+
+    def macro_dt(self):
+        v = c_double()
+        self._check(self.lib.hmm_macro_dt(self.h, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

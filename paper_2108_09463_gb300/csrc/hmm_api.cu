@@ -1,0 +1,779 @@
+// Host side of the C ABI declared in include/hmm.h.
+//
+// hmm_init validates the problem, builds the smoothing kernels exactly (moment
+// conditions of Section 2.3's Definition solved in 128-bit rationals from
+// Beta-function moments), the quadrature tables, every box's geometry and
+// micro time step (eq. Cstab with the HeunP limit on the eigenvalue ray of
+// Section 3.2), sorts boxes longest first, and allocates the per-CTA arenas.
+// hmm_micro_batch launches the persistent micro kernel; hmm_macro_step drives
+// RK4P start-up steps and graph-captured MPEA steps (Section 3.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/hmm.h"
+#include "hmm_internal.cuh"
+
+using namespace hmm;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+// ---------------------------------------------------------------- rationals
+struct Rat {
+  __int128 n, d;  // d > 0, gcd(n, d) = 1
+};
+
+__int128 gcd128(__int128 a, __int128 b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b != 0) {
+    __int128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool rat_make(__int128 n, __int128 d, Rat* r) {
+  if (d == 0) return false;
+  if (d < 0) { n = -n; d = -d; }
+  __int128 g = gcd128(n, d);
+  if (g == 0) g = 1;
+  r->n = n / g;
+  r->d = d / g;
+  return true;
+}
+
+bool mul128(__int128 a, __int128 b, __int128* out) { return !__builtin_mul_overflow(a, b, out); }
+
+bool rat_mul(const Rat& a, const Rat& b, Rat* r) {
+  // cross-reduce first to keep the numbers small
+  __int128 g1 = gcd128(a.n, b.d), g2 = gcd128(b.n, a.d);
+  if (g1 == 0) g1 = 1;
+  if (g2 == 0) g2 = 1;
+  __int128 n, d;
+  if (!mul128(a.n / g1, b.n / g2, &n) || !mul128(a.d / g2, b.d / g1, &d)) return false;
+  return rat_make(n, d, r);
+}
+
+bool rat_add(const Rat& a, const Rat& b, Rat* r) {
+  __int128 g = gcd128(a.d, b.d);
+  __int128 x, y, d;
+  if (!mul128(a.n, b.d / g, &x) || !mul128(b.n, a.d / g, &y) || !mul128(a.d / g, b.d, &d)) return false;
+  __int128 n;
+  if (__builtin_add_overflow(x, y, &n)) return false;
+  return rat_make(n, d, r);
+}
+
+bool rat_div(const Rat& a, const Rat& b, Rat* r) {
+  if (b.n == 0) return false;
+  Rat inv;
+  if (!rat_make(b.d, b.n, &inv)) return false;
+  return rat_mul(a, inv, r);
+}
+
+long double rat_ld(const Rat& a) { return (long double)a.n / (long double)a.d; }
+
+// Beta-function moments as exact rationals.
+//  two-sided: int_{-1}^{1} (1-x^2)^{q+1} x^n dx = B((n+1)/2, q+2) for even n (0 for odd n)
+//             = (q+1)! 2^{q+2} / prod_{i=0}^{q+1} (n+1+2i)
+//  one-sided: int_0^1 t^{q+1+n} (1-t)^{q+1} dt = B(q+2+n, q+2) = (q+1+n)! (q+1)! / (2q+3+n)!
+bool moment_two_sided(int q, int n, Rat* r) {
+  if (n % 2) return rat_make(0, 1, r);
+  Rat acc;
+  rat_make(1, 1, &acc);
+  for (int i = 1; i <= q + 1; ++i) {
+    Rat f;
+    rat_make(i, 1, &f);
+    if (!rat_mul(acc, f, &acc)) return false;
+  }
+  for (int i = 0; i <= q + 1; ++i) {
+    Rat f;
+    rat_make(2, n + 1 + 2 * i, &f);
+    if (!rat_mul(acc, f, &acc)) return false;
+  }
+  *r = acc;
+  return true;
+}
+
+bool moment_one_sided(int q, int n, Rat* r) {
+  Rat acc;
+  rat_make(1, 1, &acc);
+  // (q+1+n)! (q+1)! / (2q+3+n)! = (q+1)! / prod_{i=q+2+n}^{2q+3+n} i
+  for (int i = 1; i <= q + 1; ++i) {
+    Rat f;
+    rat_make(i, 1, &f);
+    if (!rat_mul(acc, f, &acc)) return false;
+  }
+  for (int i = q + 2 + n; i <= 2 * q + 3 + n; ++i) {
+    Rat f;
+    rat_make(1, i, &f);
+    if (!rat_mul(acc, f, &acc)) return false;
+  }
+  *r = acc;
+  return true;
+}
+
+// Solve sum_k c_k mom(k + r) = delta_{r0}, r = 0..p, in exact rationals.
+bool solve_kernel(int p, int q, bool one_sided, std::vector<double>* out) {
+  const int n = p + 1;
+  std::vector<std::vector<Rat>> A(n, std::vector<Rat>(n + 1));
+  for (int r = 0; r < n; ++r) {
+    for (int k = 0; k < n; ++k) {
+      bool ok = one_sided ? moment_one_sided(q, k + r, &A[r][k]) : moment_two_sided(q, k + r, &A[r][k]);
+      if (!ok) return false;
+    }
+    rat_make(r == 0 ? 1 : 0, 1, &A[r][n]);
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = -1;
+    for (int r = col; r < n; ++r)
+      if (A[r][col].n != 0) { piv = r; break; }
+    if (piv < 0) return false;
+    std::swap(A[col], A[piv]);
+    for (int r = 0; r < n; ++r) {
+      if (r == col || A[r][col].n == 0) continue;
+      Rat fac;
+      if (!rat_div(A[r][col], A[col][col], &fac)) return false;
+      for (int c = col; c <= n; ++c) {
+        Rat t;
+        if (!rat_mul(fac, A[col][c], &t)) return false;
+        t.n = -t.n;
+        if (!rat_add(A[r][c], t, &A[r][c])) return false;
+      }
+    }
+  }
+  out->resize(n);
+  for (int i = 0; i < n; ++i) {
+    Rat c;
+    if (!rat_div(A[i][n], A[i][i], &c)) return false;
+    (*out)[i] = (double)rat_ld(c);
+  }
+  return true;
+}
+
+double eval_kernel(const std::vector<double>& c, int q, double x) {  // K, support (-1, 1)
+  if (!(std::fabs(x) < 1.0)) return 0.0;
+  double poly = 0.0;
+  for (int k = (int)c.size() - 1; k >= 0; --k) poly = poly * x + c[k];
+  return std::pow(1.0 - x * x, q + 1) * poly;
+}
+
+double eval_kernel0(const std::vector<double>& c, int q, double t) {  // K0, support (0, 1)
+  if (!(t > 0.0 && t < 1.0)) return 0.0;
+  double poly = 0.0;
+  for (int k = (int)c.size() - 1; k >= 0; --k) poly = poly * t + c[k];
+  return std::pow(t * (1.0 - t), q + 1) * poly;
+}
+
+// Largest s with |1 + z + z^2/2| <= 1 on z = s(-alpha + i): |R|^2 - 1 = s g(s) with
+// g(s) = (1+a^2)^2/4 s^3 - a(1+a^2) s^2 + 2 a^2 s - 2a; its smallest positive root.
+double heun_limit(double a) {
+  auto g = [a](double s) {
+    const double b = 1.0 + a * a;
+    return ((0.25 * b * b * s - a * b) * s + 2.0 * a * a) * s - 2.0 * a;
+  };
+  double lo = 0.0, hi = 1e-3;
+  while (g(hi) < 0.0) {
+    lo = hi;
+    hi += 1e-3;
+    if (hi > 20.0) return 0.0;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (g(mid) < 0.0) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr double kMacroDtConstant = 0.06;
+
+}  // namespace
+
+// ---------------------------------------------------------------- handle
+struct HmmHandle {
+  hmm_params p{};
+  std::vector<hmm_coef_term> terms;
+  std::vector<double> eps_field;
+  std::vector<int> n_field;
+  int dim = 0, P = 0, nmac[3] = {1, 1, 1};
+  double DX[3] = {0, 0, 0};
+  int radius = 3, interp_k = 2;
+  double a_max = 0;
+  cudaStream_t user_stream = nullptr;  // the caller's stream (may be the legacy stream)
+  cudaStream_t stream = nullptr;       // the library's own non-blocking stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int device = 0, num_sms = 0;
+  // host copies
+  std::vector<BoxDesc> boxes;      // sorted longest first
+  std::vector<double> box_dt, box_mu, box_dx;
+  std::vector<int> box_n;
+  double lu_per_batch = 0;
+  int nmax = 0;
+  double dt_macro = 0;
+  // device
+  BoxDesc* d_boxes = nullptr;
+  double* d_W64 = nullptr;
+  float* d_W32 = nullptr;
+  double* d_w64 = nullptr;
+  float* d_w32 = nullptr;
+  char* d_arena = nullptr;
+  size_t slot_bytes = 0;
+  int grid = 0, block = 256;
+  size_t smem = 0;
+  bool res2d = false;        // resident 2D FP32 kernel
+  int* d_queue = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;      // pinned
+  double* d_H = nullptr;     // 3P
+  double* d_hist = nullptr;  // 2 x 3P
+  double* d_acc = nullptr;   // 3P (RK4 accumulator)
+  double* d_stage = nullptr; // 3P (RK4 stage state)
+  double* d_Mhost = nullptr; // 3P (host-buffer entry points)
+  double* d_Hhost = nullptr; // 3P
+  long long j = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double last_ms = 0;
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_M = nullptr;
+  std::string err;
+  MicroArgs args{};
+};
+
+namespace {
+
+hmm_status fail(HmmHandle* h, hmm_status s, const std::string& msg) {
+  if (h) h->err = msg; else g_init_error = msg;
+  return s;
+}
+
+hmm_status cuda_fail(HmmHandle* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? HMM_ERR_OUT_OF_MEMORY : HMM_ERR_CUDA, m);
+}
+
+#define HMM_CUDA(h, call)                                    \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+void free_all(HmmHandle* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_arena, h->d_queue,
+                  h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->stream) cudaStreamDestroy(h->stream);
+}
+
+int max_n_for_dim(int d) { return d == 1 ? 1024 : (d == 2 ? 256 : 64); }
+
+hmm_status build(HmmHandle* h) {
+  hmm_params& p = h->p;
+  if (p.dim < 1 || p.dim > 3) return fail(h, HMM_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
+  for (int i = 0; i < 4; ++i)
+    if (p.reserved[i] != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  h->dim = p.dim;
+  if (!(p.L > 0)) p.L = 1.0;
+  if (p.px <= 0) p.px = 3;
+  if (p.qx <= 0) p.qx = 7;
+  if (p.pt <= 0) p.pt = 3;
+  if (p.qt <= 0) p.qt = 7;
+  if (p.interp_order <= 0) p.interp_order = 4;
+  if (p.stencil_order <= 0) p.stencil_order = 4;
+  if (!(p.dt_safety > 0)) p.dt_safety = 0.8;
+  if (p.interp_order != 2 && p.interp_order != 4)
+    return fail(h, HMM_ERR_INVALID_ARG, "interp_order must be 2 or 4");
+  if (p.stencil_order != 2 && p.stencil_order != 4)
+    return fail(h, HMM_ERR_INVALID_ARG, "stencil_order must be 2 or 4");
+  if (p.precision != HMM_FP64_PLAIN && p.precision != HMM_FP32_BATCHED)
+    return fail(h, HMM_ERR_INVALID_ARG, "precision must be HMM_FP64_PLAIN or HMM_FP32_BATCHED");
+  if (p.kernel_variant < 0 || p.kernel_variant > 2)
+    return fail(h, HMM_ERR_INVALID_ARG, "kernel_variant must be 0, 1 or 2");
+  if (!(p.alpha > 0 && p.alpha <= 1)) return fail(h, HMM_ERR_INVALID_ARG, "alpha must be in (0, 1] (A2)");
+  if (!(p.alpha_micro > 0 && p.alpha_micro <= 4))
+    return fail(h, HMM_ERR_INVALID_ARG, "alpha_micro must be in (0, 4]");
+  if (p.n_terms < 0 || p.n_terms > kMaxTerms) return fail(h, HMM_ERR_INVALID_ARG, "n_terms must be 0..8");
+  if (p.n_terms > 0 && !p.terms) return fail(h, HMM_ERR_INVALID_ARG, "terms is NULL");
+  if (!(p.pts_per_eps > 0)) return fail(h, HMM_ERR_INVALID_ARG, "pts_per_eps must be > 0");
+  if (p.micro_steps < 1 || p.micro_steps > 1000000) return fail(h, HMM_ERR_INVALID_ARG, "micro_steps out of range");
+  if (p.px > 6 || p.pt > 6 || p.qx > 12 || p.qt > 12)
+    return fail(h, HMM_ERR_INVALID_ARG, "kernel parameters must satisfy p <= 6, q <= 12");
+  h->radius = p.stencil_order == 2 ? 1 : 3;
+  h->interp_k = p.interp_order / 2;
+  long long P = 1;
+  for (int k = 0; k < h->dim; ++k) {
+    if (p.n_macro[k] < 2 * h->interp_k + 1)
+      return fail(h, HMM_ERR_INVALID_ARG, "n_macro must be >= interp_order + 1 on every axis");
+    h->nmac[k] = p.n_macro[k];
+    h->DX[k] = p.L / p.n_macro[k];
+    P *= p.n_macro[k];
+  }
+  if (P > (1LL << 30)) return fail(h, HMM_ERR_INVALID_ARG, "too many macro points");
+  h->P = (int)P;
+  h->terms.assign(p.terms, p.terms + p.n_terms);
+  for (const auto& t : h->terms)
+    for (int k = 0; k < 3; ++k) {
+      if (t.kind[k] < 0 || t.kind[k] > 2 || t.scale[k] < 0 || t.scale[k] > 1)
+        return fail(h, HMM_ERR_INVALID_ARG, "coefficient term kind/scale out of range");
+      if (k >= h->dim && t.kind[k] != 0)
+        return fail(h, HMM_ERR_INVALID_ARG, "coefficient factor on an axis beyond dim");
+    }
+  p.terms = nullptr;
+  if (p.eps_field) h->eps_field.assign(p.eps_field, p.eps_field + h->P);
+  if (p.box_n_field) h->n_field.assign(p.box_n_field, p.box_n_field + h->P);
+  p.eps_field = nullptr;
+  p.box_n_field = nullptr;
+  h->a_max = p.c0;
+  for (const auto& t : h->terms) h->a_max += std::fabs(t.amp);
+  if (!(h->a_max > 0)) return fail(h, HMM_ERR_INVALID_ARG, "coefficient upper bound must be positive");
+
+  // Smoothing kernels (exact rationals).
+  std::vector<double> cK, cK0;
+  if (!solve_kernel(p.px, p.qx, false, &cK) || !solve_kernel(p.pt, p.qt, true, &cK0))
+    return fail(h, HMM_ERR_INVALID_ARG, "kernel moment system overflowed 128-bit rationals");
+
+  // Time weights w_n = K0(n/M), normalised to sum 1.
+  const int M = p.micro_steps;
+  std::vector<double> w(M + 1);
+  double ws = 0;
+  for (int n = 0; n <= M; ++n) ws += (w[n] = eval_kernel0(cK0, p.qt, (double)n / (double)M));
+  if (!(ws != 0)) return fail(h, HMM_ERR_INVALID_ARG, "time weights vanish");
+  for (auto& v : w) v /= ws;
+
+  // Boxes.
+  const double smax = heun_limit(p.alpha_micro);
+  const double lam = p.stencil_order == 2 ? 4.0 : (28.0 / 12.0) * (28.0 / 12.0);
+  const int nlim = max_n_for_dim(h->dim);
+  std::map<int, int> class_ofs;
+  std::vector<double> W64;
+  h->boxes.resize(h->P);
+  h->box_dt.resize(h->P);
+  h->box_mu.resize(h->P);
+  h->box_dx.resize(h->P);
+  h->box_n.resize(h->P);
+  h->nmax = 0;
+  h->lu_per_batch = 0;
+  for (int pi = 0; pi < h->P; ++pi) {
+    BoxDesc bd{};
+    bd.p = pi;
+    int rem = pi;
+    for (int k = h->dim - 1; k >= 0; --k) {
+      bd.ci[k] = rem % h->nmac[k];
+      rem /= h->nmac[k];
+    }
+    for (int k = 0; k < h->dim; ++k) bd.xc[k] = bd.ci[k] * h->DX[k];
+    bd.eps = h->eps_field.empty() ? p.eps : h->eps_field[pi];
+    bd.N = h->n_field.empty() ? p.box_n : h->n_field[pi];
+    if (!(bd.eps > 0)) return fail(h, HMM_ERR_INVALID_ARG, "eps must be > 0");
+    if (bd.N < 2 * h->radius + 2 || bd.N > nlim)
+      return fail(h, HMM_ERR_INVALID_ARG, "box_n out of range for this dimension and stencil");
+    bd.dx = bd.eps / p.pts_per_eps;
+    const double mup = (bd.N - 1) * bd.dx / 2.0;
+    const double mu = p.mu_over_eps > 0 ? p.mu_over_eps * bd.eps : 0.8 * mup;
+    const double omega = h->a_max * h->dim * lam / (bd.dx * bd.dx);
+    bd.dt = p.dt_safety * smax / omega;
+    if (!(bd.dt > 0)) return fail(h, HMM_ERR_INVALID_ARG, "micro time step is not positive");
+    auto it = class_ofs.find(bd.N);
+    if (it == class_ofs.end()) {
+      // spatial weights W_j = K(xi_j/mu), normalised; xi_j = (j - (N-1)/2) dx
+      const int ofs = (int)W64.size();
+      double s = 0;
+      for (int jn = 0; jn < bd.N; ++jn) {
+        const double xi = (jn - (bd.N - 1) / 2.0) * bd.dx;
+        const double v = eval_kernel(cK, p.qx, xi / mu);
+        W64.push_back(v);
+        s += v;
+      }
+      if (!(s != 0)) return fail(h, HMM_ERR_INVALID_ARG, "spatial weights vanish (mu too small)");
+      for (int jn = 0; jn < bd.N; ++jn) W64[ofs + jn] /= s;
+      for (int jn = 0; jn < h->radius; ++jn)
+        if (W64[ofs + jn] != 0.0 || W64[ofs + bd.N - 1 - jn] != 0.0)
+          return fail(h, HMM_ERR_INVALID_ARG, "averaging box [-mu, mu] reaches the Dirichlet ring");
+      it = class_ofs.emplace(bd.N, ofs).first;
+    }
+    bd.wofs = it->second;
+    h->boxes[pi] = bd;
+    h->box_dt[pi] = bd.dt;
+    h->box_mu[pi] = mu;
+    h->box_dx[pi] = bd.dx;
+    h->box_n[pi] = bd.N;
+    h->nmax = std::max(h->nmax, bd.N);
+    double lu = M;
+    for (int k = 0; k < h->dim; ++k) lu *= (bd.N - 2 * h->radius);
+    h->lu_per_batch += lu;
+  }
+  std::stable_sort(h->boxes.begin(), h->boxes.end(),
+                   [](const BoxDesc& x, const BoxDesc& y) { return x.N > y.N; });
+  if (p.dt_macro > 0) {
+    h->dt_macro = p.dt_macro;
+  } else {
+    double dX = h->DX[0];
+    for (int k = 1; k < h->dim; ++k) dX = std::min(dX, h->DX[k]);
+    h->dt_macro = kMacroDtConstant * dX * dX / (h->dim * h->a_max);
+  }
+
+  // Device side.
+  HMM_CUDA(h, cudaGetDevice(&h->device));
+  HMM_CUDA(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  std::vector<float> W32(W64.begin(), W64.end()), w32(w.begin(), w.end());
+  HMM_CUDA(h, cudaMalloc(&h->d_boxes, sizeof(BoxDesc) * h->P));
+  HMM_CUDA(h, cudaMalloc(&h->d_W64, sizeof(double) * W64.size()));
+  HMM_CUDA(h, cudaMalloc(&h->d_W32, sizeof(float) * W32.size()));
+  HMM_CUDA(h, cudaMalloc(&h->d_w64, sizeof(double) * w.size()));
+  HMM_CUDA(h, cudaMalloc(&h->d_w32, sizeof(float) * w32.size()));
+  HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->P, cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_W64, W64.data(), sizeof(double) * W64.size(), cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_W32, W32.data(), sizeof(float) * W32.size(), cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_w64, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_w32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMalloc(&h->d_queue, sizeof(int)));
+  HMM_CUDA(h, cudaMalloc(&h->d_err, sizeof(int)));
+  HMM_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+  HMM_CUDA(h, cudaMallocHost(&h->h_err, sizeof(int)));
+  const size_t f3 = sizeof(double) * 3 * (size_t)h->P;
+  HMM_CUDA(h, cudaMalloc(&h->d_H, f3));
+  HMM_CUDA(h, cudaMalloc(&h->d_hist, 2 * f3));
+  HMM_CUDA(h, cudaMemset(h->d_hist, 0, 2 * f3));
+  HMM_CUDA(h, cudaMalloc(&h->d_acc, f3));
+  HMM_CUDA(h, cudaMalloc(&h->d_stage, f3));
+  HMM_CUDA(h, cudaEventCreate(&h->ev0));
+  HMM_CUDA(h, cudaEventCreate(&h->ev1));
+  HMM_CUDA(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  HMM_CUDA(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  HMM_CUDA(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+
+  // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
+  int optin = 0;
+  HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim == 2 && h->nmax - 2 * h->radius <= 64 &&
+                      res2d_smem_bytes(h->nmax, h->radius) + 64 <= (size_t)optin &&
+                      res2d_setup_fits(h->nmax, h->radius, h->interp_k, p.n_terms);
+  if (p.kernel_variant == 2 && !res_ok)
+    return fail(h, HMM_ERR_INVALID_ARG, "the resident kernel needs FP32, d = 2 and N - 2r <= 64");
+  h->res2d = res_ok && p.kernel_variant == 2;
+
+  // Launch shape: persistent grid of (CTAs per SM x SMs), capped by the box count.
+  int per_sm = 0;
+  if (h->res2d) {
+    h->block = res2d_block(h->nmax, h->radius);
+    h->smem = res2d_smem_bytes(h->nmax, h->radius);
+    HMM_CUDA(h, prepare_micro_fp32_2d(h->radius, h->smem, &per_sm));
+    h->slot_bytes = res2d_slot_bytes(h->nmax);
+  } else {
+    h->block = 256;
+    h->smem = micro_smem_bytes(h->dim, h->nmax, h->interp_k, p.n_terms);
+    HMM_CUDA(h, p.precision == HMM_FP64_PLAIN
+                    ? prepare_micro_fp64(h->dim, h->radius, h->block, h->smem, &per_sm)
+                    : prepare_micro_fp32(h->dim, h->radius, h->block, h->smem, &per_sm));
+    h->slot_bytes = p.precision == HMM_FP64_PLAIN ? micro_slot_bytes_fp64(h->dim, h->nmax)
+                                                  : micro_slot_bytes_fp32(h->dim, h->nmax);
+  }
+  if (per_sm < 1) return fail(h, HMM_ERR_INVALID_ARG, "micro kernel does not fit on an SM for this box size");
+  h->grid = std::min(h->P, per_sm * h->num_sms);
+  HMM_CUDA(h, cudaMalloc(&h->d_arena, h->slot_bytes * (size_t)h->grid));
+
+  MicroArgs& a = h->args;
+  a.boxes = h->d_boxes;
+  a.n_boxes = h->P;
+  a.queue = h->d_queue;
+  a.err = h->d_err;
+  a.P = h->P;
+  for (int k = 0; k < 3; ++k) {
+    a.nmac[k] = h->nmac[k];
+    a.DX[k] = h->DX[k];
+  }
+  a.interp_k = h->interp_k;
+  a.msteps = M;
+  a.alpha_micro = p.alpha_micro;
+  a.W64 = h->d_W64;
+  a.W32 = h->d_W32;
+  a.w64 = h->d_w64;
+  a.w32 = h->d_w32;
+  a.c0 = p.c0;
+  a.n_terms = p.n_terms;
+  for (int t = 0; t < p.n_terms; ++t) {
+    const auto& s = h->terms[t];
+    TermDev& d = a.terms[t];
+    d.amp = s.amp;
+    for (int k = 0; k < 3; ++k) {
+      d.kind[k] = s.kind[k];
+      d.scale[k] = s.scale[k];
+      d.omega[k] = s.omega[k];
+      d.phase[k] = s.phase[k];
+    }
+  }
+  a.arena = h->d_arena;
+  a.slot_bytes = h->slot_bytes;
+  a.nmax = h->nmax;
+  return HMM_OK;
+}
+
+// Enqueue one micro batch (no synchronisation).
+hmm_status enqueue_micro(HmmHandle* h, const double* M, double* Havg) {
+  HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+  MicroArgs a = h->args;
+  a.M = M;
+  a.Havg = Havg;
+  cudaError_t e = h->res2d ? launch_micro_fp32_2d(a, h->radius, h->grid, h->block, h->smem, h->stream)
+                 : h->p.precision == HMM_FP64_PLAIN
+                      ? launch_micro_fp64(a, h->dim, h->radius, h->grid, h->block, h->smem, h->stream)
+                      : launch_micro_fp32(a, h->dim, h->radius, h->grid, h->block, h->smem, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "micro kernel launch");
+  return HMM_OK;
+}
+
+hmm_status check_error_word(HmmHandle* h) {
+  HMM_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int e = *h->h_err;
+  if (e) {
+    HMM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (e & kErrCoefNonPositive) return fail(h, HMM_ERR_INVALID_ARG, "coefficient a^eps <= 0 at a micro face (A1)");
+    return fail(h, HMM_ERR_NONFINITE, "non-finite value in the micro solve or macro state");
+  }
+  return HMM_OK;
+}
+
+hmm_status enqueue_mpea_step(HmmHandle* h, double* M) {
+  hmm_status s = enqueue_micro(h, M, h->d_H);
+  if (s != HMM_OK) return s;
+  cudaError_t e = launch_mpea_update(M, h->d_H, h->d_hist, h->p.alpha, h->dt_macro, h->P, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mpea kernel launch");
+  return HMM_OK;
+}
+
+hmm_status enqueue_rk4_step(HmmHandle* h, double* M) {
+  const double* states[4] = {M, h->d_stage, h->d_stage, h->d_stage};
+  for (int stage = 1; stage <= 4; ++stage) {
+    hmm_status s = enqueue_micro(h, states[stage - 1], h->d_H);
+    if (s != HMM_OK) return s;
+    double* next = stage == 4 ? M : h->d_stage;
+    cudaError_t e = launch_rk4_stage(M, states[stage - 1], h->d_H, h->p.alpha, h->dt_macro, stage,
+                                     h->d_acc, next, h->d_hist, h->P, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rk4 stage launch");
+  }
+  return HMM_OK;
+}
+
+hmm_status ensure_graph(HmmHandle* h, double* M) {
+  if (h->graph && h->graph_M == M) return HMM_OK;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  cudaGraph_t g;
+  HMM_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  hmm_status s = enqueue_mpea_step(h, M);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (s != HMM_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  h->graph_M = M;
+  return HMM_OK;
+}
+
+HmmHandle* as_handle(void* p) { return static_cast<HmmHandle*>(p); }
+
+// Order the library's stream after the work already queued on the caller's stream.
+hmm_status begin_call(HmmHandle* h) {
+  HMM_CUDA(h, cudaEventRecord(h->ev_in, h->user_stream));
+  HMM_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  return HMM_OK;
+}
+
+// Order the caller's stream after the library's work.
+hmm_status end_call(HmmHandle* h) {
+  HMM_CUDA(h, cudaEventRecord(h->ev_out, h->stream));
+  HMM_CUDA(h, cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+  return HMM_OK;
+}
+
+#define HMM_TRY(expr)                 \
+  do {                                \
+    hmm_status s_ = (expr);           \
+    if (s_ != HMM_OK) return s_;      \
+  } while (0)
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+hmm_status hmm_init(const hmm_params* params, void* cuda_stream, void** handle_out) {
+  g_init_error.clear();
+  if (!params || !handle_out) return fail(nullptr, HMM_ERR_INVALID_ARG, "null params or handle_out");
+  *handle_out = nullptr;
+  HmmHandle* h = new (std::nothrow) HmmHandle();
+  if (!h) return fail(nullptr, HMM_ERR_OUT_OF_MEMORY, "host allocation failed");
+  h->p = *params;
+  h->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  hmm_status s = build(h);
+  if (s != HMM_OK) {
+    g_init_error = h->err;
+    free_all(h);
+    delete h;
+    return s;
+  }
+  *handle_out = h;
+  return HMM_OK;
+}
+
+hmm_status hmm_micro_batch(void* handle, const double* M_dev, double* Havg_dev) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_dev || !Havg_dev) return fail(h, HMM_ERR_INVALID_ARG, "null device pointer");
+  HMM_TRY(begin_call(h));
+  HMM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  hmm_status s = enqueue_micro(h, M_dev, Havg_dev);
+  if (s != HMM_OK) return s;
+  HMM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  HMM_TRY(end_call(h));
+  s = check_error_word(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->last_ms = ms;
+  return s;
+}
+
+hmm_status hmm_micro_batch_host(void* handle, const double* M_host, double* Havg_host) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_host || !Havg_host) return fail(h, HMM_ERR_INVALID_ARG, "null host pointer");
+  const size_t f3 = sizeof(double) * 3 * (size_t)h->P;
+  if (!h->d_Mhost) HMM_CUDA(h, cudaMalloc(&h->d_Mhost, f3));
+  if (!h->d_Hhost) HMM_CUDA(h, cudaMalloc(&h->d_Hhost, f3));
+  HMM_TRY(begin_call(h));
+  HMM_CUDA(h, cudaMemcpyAsync(h->d_Mhost, M_host, f3, cudaMemcpyHostToDevice, h->stream));
+  hmm_status s = enqueue_micro(h, h->d_Mhost, h->d_Hhost);
+  if (s != HMM_OK) return s;
+  HMM_CUDA(h, cudaMemcpyAsync(Havg_host, h->d_Hhost, f3, cudaMemcpyDeviceToHost, h->stream));
+  return check_error_word(h);
+}
+
+hmm_status hmm_macro_step(void* handle, double* M_dev, int n_steps) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_dev || n_steps < 0) return fail(h, HMM_ERR_INVALID_ARG, "null M_dev or negative n_steps");
+  HMM_TRY(begin_call(h));
+  for (int s = 0; s < n_steps; ++s) {
+    hmm_status st;
+    if (h->j < 2) {
+      st = enqueue_rk4_step(h, M_dev);
+    } else {
+      st = ensure_graph(h, M_dev);
+      if (st == HMM_OK) {
+        cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+      }
+    }
+    if (st != HMM_OK) return st;
+    h->j += 1;
+  }
+  cudaError_t e = launch_check_finite(M_dev, 3 * h->P, h->d_err, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "finite check launch");
+  HMM_TRY(end_call(h));
+  return check_error_word(h);
+}
+
+hmm_status hmm_macro_step_host(void* handle, double* M_host, int n_steps) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_host) return fail(h, HMM_ERR_INVALID_ARG, "null host pointer");
+  const size_t f3 = sizeof(double) * 3 * (size_t)h->P;
+  if (!h->d_Mhost) HMM_CUDA(h, cudaMalloc(&h->d_Mhost, f3));
+  HMM_CUDA(h, cudaMemcpyAsync(h->d_Mhost, M_host, f3, cudaMemcpyHostToDevice, h->stream));
+  hmm_status s = hmm_macro_step(handle, h->d_Mhost, n_steps);
+  if (s != HMM_OK) return s;
+  HMM_CUDA(h, cudaMemcpyAsync(M_host, h->d_Mhost, f3, cudaMemcpyDeviceToHost, h->stream));
+  HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HMM_OK;
+}
+
+hmm_status hmm_get_state(void* handle, double* hist_dev, long long* j) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (hist_dev) {
+    HMM_TRY(begin_call(h));
+    HMM_CUDA(h, cudaMemcpyAsync(hist_dev, h->d_hist, sizeof(double) * 6 * (size_t)h->P,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  if (j) *j = h->j;
+  return HMM_OK;
+}
+
+hmm_status hmm_set_state(void* handle, const double* hist_dev, long long j) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (j < 0) return fail(h, HMM_ERR_INVALID_ARG, "negative step count");
+  if (hist_dev) {
+    HMM_TRY(begin_call(h));
+    HMM_CUDA(h, cudaMemcpyAsync(h->d_hist, hist_dev, sizeof(double) * 6 * (size_t)h->P,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+  } else if (j >= 1) {
+    return fail(h, HMM_ERR_INVALID_ARG, "a step count >= 1 needs the history");
+  }
+  h->j = j;
+  return HMM_OK;
+}
+
+hmm_status hmm_stats(void* handle, double* lattice_updates_per_batch, double* last_batch_ms) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (lattice_updates_per_batch) *lattice_updates_per_batch = h->lu_per_batch;
+  if (last_batch_ms) *last_batch_ms = h->last_ms;
+  return HMM_OK;
+}
+
+hmm_status hmm_box_info(void* handle, double* dt, double* mu, double* dx, int* n) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (dt) std::memcpy(dt, h->box_dt.data(), sizeof(double) * h->P);
+  if (mu) std::memcpy(mu, h->box_mu.data(), sizeof(double) * h->P);
+  if (dx) std::memcpy(dx, h->box_dx.data(), sizeof(double) * h->P);
+  if (n) std::memcpy(n, h->box_n.data(), sizeof(int) * h->P);
+  return HMM_OK;
+}
+
+hmm_status hmm_macro_dt(void* handle, double* dt_macro) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!dt_macro) return fail(h, HMM_ERR_INVALID_ARG, "null pointer");
+  *dt_macro = h->dt_macro;
+  return HMM_OK;
+}
+
+const char* hmm_last_error(void* handle) {
+  HmmHandle* h = as_handle(handle);
+  return h ? h->err.c_str() : g_init_error.c_str();
+}
+
+void hmm_destroy(void* handle) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace hmm {
+
+constexpr int kMaxTerms = 8;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// Error bits raised by kernels in the device error word.
+enum : int { kErrNonFinite = 1, kErrCoefNonPositive = 2, kErrConfig = 4 };
+
+struct TermDev {
+  double amp;
+  int kind[3];
+  int scale[3];
+  double omega[3];
+  double phase[3];
+};
+
+// One micro problem (one macro point). Sorted longest-first in the work queue.
+struct BoxDesc {
+  int p;        // macro point (C-order linear index)
+  int ci[3];    // macro multi-index
+  int N;        // micro nodes per axis, Dirichlet ring included
+  int wofs;     // offset of this box's spatial weight table (length N)
+  double eps;   // eps_i
+  double dx;    // micro grid spacing
+  double dt;    // micro time step
+  double xc[3]; // macro point coordinates x_i
+};
+
+struct MicroArgs {
+  const BoxDesc* boxes;
+  int n_boxes;
+  int* queue;            // work counter (reset to 0 before each launch)
+  int* err;              // error word (bits above)
+  const double* M;       // macro field, SoA 3 x P
+  double* Havg;          // output, SoA 3 x P
+  int P;
+  int nmac[3];
+  double DX[3];
+  int interp_k;          // k of Q_[2k]
+  int msteps;            // M micro steps
+  double alpha_micro;
+  const double* W64;     // spatial weight tables (per size class)
+  const float* W32;
+  const double* w64;     // time weights, msteps + 1
+  const float* w32;
+  double c0;
+  int n_terms;
+  TermDev terms[kMaxTerms];
+  char* arena;           // per-CTA scratch
+  size_t slot_bytes;
+  int nmax;              // largest N of the batch (sizes the arena and tables)
+};
+
+// Launchers (one per precision); dim in {1,2,3}, radius in {1,3}.
+cudaError_t launch_micro_fp64(const MicroArgs& a, int dim, int radius, int grid, int block,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_micro_fp32(const MicroArgs& a, int dim, int radius, int grid, int block,
+                              size_t smem, cudaStream_t st);
+// Per-CTA arena bytes for boxes of up to nmax nodes per axis.
+size_t micro_slot_bytes_fp64(int dim, int nmax);
+size_t micro_slot_bytes_fp32(int dim, int nmax);
+// Dynamic shared memory of the set-up tables.
+size_t micro_smem_bytes(int dim, int nmax, int interp_k, int n_terms);
+// Set the kernel's dynamic shared-memory limit and return resident CTAs per SM.
+cudaError_t prepare_micro_fp64(int dim, int radius, int block, size_t smem, int* ctas_per_sm);
+cudaError_t prepare_micro_fp32(int dim, int radius, int block, size_t smem, int* ctas_per_sm);
+
+// Resident 2D FP32 kernel (micro_fp32_2d.cu).
+size_t res2d_smem_bytes(int nmax, int R);
+bool res2d_setup_fits(int nmax, int R, int interp_k, int n_terms);
+size_t res2d_slot_bytes(int nmax);
+int res2d_block(int nmax, int R);
+cudaError_t prepare_micro_fp32_2d(int radius, size_t smem, int* ctas_per_sm);
+cudaError_t launch_micro_fp32_2d(const MicroArgs& a, int radius, int grid, int block, size_t smem,
+                                 cudaStream_t st);
+
+// Macro-side kernels (FP64, pointwise over P points).
+cudaError_t launch_h_term(const double* M, const double* H, double alpha, double* h, int P,
+                          cudaStream_t st);
+cudaError_t launch_mpea_update(double* M, const double* H, double* hist, double alpha,
+                               double dt, int P, cudaStream_t st);
+// RK4P: k = f(Ms, H); acc += wk*k (acc = 0 when first); Mnext = normalise(M + c*k).
+cudaError_t launch_rk4_stage(const double* M, const double* Ms, const double* H, double alpha,
+                             double dt, int stage, double* acc, double* Mnext, double* hist0,
+                             int P, cudaStream_t st);
+cudaError_t launch_check_finite(const double* x, int n, int* err, cudaStream_t st);
+
+}  // namespace hmm

@@ -1,0 +1,138 @@
+// Macro-side kernels of the field model (Section 2.2, eq. macro_disc), FP64,
+// one thread per macro point:
+//  - MPEA: h^j = H + alpha M x H (eq. h_term), h^{j+1/2} = 23/12 h^j - 16/12
+//    h^{j-1} + 5/12 h^{j-2} (eq. h_mpea), and the midpoint update
+//    (M' - M)/dt = -(M + M')/2 x h^{j+1/2} (eq. mpe_update), solved in closed
+//    form: with w = dt/2 h, (I - [w]x) M' = (I + [w]x) M, whose solution is
+//    M' = M + 2/(1 + |w|^2) (w x M + w x (w x M)).
+//  - RK4P stages (Section 3.1) with normalised stage states.
+#include "hmm_internal.cuh"
+
+namespace hmm {
+
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ void load3(const double* x, int P, int p, double* v) {
+  v[0] = x[p];
+  v[1] = x[P + p];
+  v[2] = x[2 * P + p];
+}
+
+__device__ __forceinline__ void store3(double* x, int P, int p, const double* v) {
+  x[p] = v[0];
+  x[P + p] = v[1];
+  x[2 * P + p] = v[2];
+}
+
+__global__ void h_term_kernel(const double* M, const double* H, double alpha, double* h, int P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double m[3], Hv[3], c[3];
+  load3(M, P, p, m);
+  load3(H, P, p, Hv);
+  cross3(m, Hv, c);
+  for (int i = 0; i < 3; ++i) c[i] = Hv[i] + alpha * c[i];
+  store3(h, P, p, c);
+}
+
+__global__ void mpea_kernel(double* M, const double* H, double* hist, double alpha, double dt, int P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double m[3], Hv[3], c[3], h1[3], h2[3], hj[3], w[3];
+  load3(M, P, p, m);
+  load3(H, P, p, Hv);
+  load3(hist, P, p, h1);
+  load3(hist + 3 * (size_t)P, P, p, h2);
+  cross3(m, Hv, c);
+  for (int i = 0; i < 3; ++i) hj[i] = Hv[i] + alpha * c[i];
+  for (int i = 0; i < 3; ++i)
+    w[i] = 0.5 * dt * ((23.0 / 12.0) * hj[i] - (16.0 / 12.0) * h1[i] + (5.0 / 12.0) * h2[i]);
+  double wm[3], wwm[3];
+  cross3(w, m, wm);
+  cross3(w, wm, wwm);
+  const double f = 2.0 / (1.0 + w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double out[3];
+  for (int i = 0; i < 3; ++i) out[i] = m[i] + f * (wm[i] + wwm[i]);
+  store3(M, P, p, out);
+  store3(hist + 3 * (size_t)P, P, p, h1);
+  store3(hist, P, p, hj);
+}
+
+// RK4P stage s (1..4). Ms: the (normalised) stage state whose micro batch gave H.
+// Stage 1 also shifts the MPEA history and stores h^j = H + alpha M x H.
+__global__ void rk4_stage_kernel(const double* M, const double* Ms, const double* H, double alpha,
+                                 double dt, int stage, double* acc, double* Mnext, double* hist,
+                                 int P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double m[3], ms[3], Hv[3], mxH[3], mmxH[3], k[3];
+  load3(M, P, p, m);
+  load3(Ms, P, p, ms);
+  load3(H, P, p, Hv);
+  cross3(ms, Hv, mxH);
+  cross3(ms, mxH, mmxH);
+  for (int i = 0; i < 3; ++i) k[i] = -mxH[i] - alpha * mmxH[i];
+  double a[3];
+  if (stage == 1) {
+    double hj[3], old[3];
+    for (int i = 0; i < 3; ++i) hj[i] = Hv[i] + alpha * mxH[i];
+    load3(hist, P, p, old);
+    store3(hist + 3 * (size_t)P, P, p, old);
+    store3(hist, P, p, hj);
+    for (int i = 0; i < 3; ++i) a[i] = k[i];
+  } else {
+    load3(acc, P, p, a);
+    const double wk = stage == 4 ? 1.0 : 2.0;
+    for (int i = 0; i < 3; ++i) a[i] += wk * k[i];
+  }
+  store3(acc, P, p, a);
+  double u[3];
+  if (stage == 4) {
+    for (int i = 0; i < 3; ++i) u[i] = m[i] + (dt / 6.0) * a[i];
+  } else {
+    const double c = stage == 3 ? dt : 0.5 * dt;
+    for (int i = 0; i < 3; ++i) u[i] = m[i] + c * k[i];
+  }
+  const double inv = 1.0 / sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  for (int i = 0; i < 3; ++i) u[i] *= inv;
+  store3(Mnext, P, p, u);
+}
+
+__global__ void check_finite_kernel(const double* x, int n, int* err) {
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonFinite);
+}
+
+static inline int nblk(int P) { return (P + 255) / 256; }
+
+cudaError_t launch_h_term(const double* M, const double* H, double alpha, double* h, int P,
+                          cudaStream_t st) {
+  h_term_kernel<<<nblk(P), 256, 0, st>>>(M, H, alpha, h, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mpea_update(double* M, const double* H, double* hist, double alpha, double dt,
+                               int P, cudaStream_t st) {
+  mpea_kernel<<<nblk(P), 256, 0, st>>>(M, H, hist, alpha, dt, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_stage(const double* M, const double* Ms, const double* H, double alpha,
+                             double dt, int stage, double* acc, double* Mnext, double* hist0,
+                             int P, cudaStream_t st) {
+  rk4_stage_kernel<<<nblk(P), 256, 0, st>>>(M, Ms, H, alpha, dt, stage, acc, Mnext, hist0, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* x, int n, int* err, cudaStream_t st) {
+  check_finite_kernel<<<64, 256, 0, st>>>(x, n, err);
+  return cudaGetLastError();
+}
+
+}  // namespace hmm

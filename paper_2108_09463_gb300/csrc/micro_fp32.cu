@@ -1,0 +1,324 @@
+// Batched FP32 micro-batch kernel (perturbation form).
+//
+// The same mathematics as the FP64 kernel, stepped in FP32 on the perturbation
+// v = m - m_init (0 on the Dirichlet ring, Section 4.2). Because the stencil is
+// linear, H(m) = H(m_init) + H(v): H(m_init) is computed once per box in FP64
+// from the FP64 m_init; the FP32 loop only sees H(v).
+//
+// Accuracy design (FP32 state, FP64 averages):
+//  * The state is carried as v = v_hi + v_lo: each step forms its whole
+//    increment (both Heun stages and the projection) in FP32, adds the carried
+//    rounding error v_lo to it, and adds that to v_hi with an exact
+//    (Fast2Sum) error term, which becomes the new v_lo. The stencil reads v_hi.
+//  * The average (eq. upscaling) sum_n w_n sum_xi W H(m^n) equals, because the
+//    discrete operator restricted to the interior is symmetric and W vanishes
+//    on the ring, (sum_n w_n) sum_xi W H(m_init) + sum_xi H(W)(xi) V(xi) with
+//    V = sum_n w_n v^n. V is accumulated per node in FP32 with Kahan
+//    compensation; H(W) and both contractions are evaluated in FP64.
+//  * The HeunP projection (Section 3.1) is applied in perturbation form: with
+//    u = m_init + v~ and s = |u|^2 - 1 (m_init taken as exactly unit, which its
+//    FP64 value is), normalise(u) - m_init = v~ + c u, c = -s/(sqrt(1+s)(1+sqrt(1+s))),
+//    so no O(1) component of m_init ever cancels in FP32.
+#include "micro_common.cuh"
+#include "stencil.cuh"
+
+namespace hmm {
+
+struct Fp32Slot {
+  double* mi64;  // [3][cap] m_init, FP64 (set-up only)
+  double* af64;  // [D][cap] face coefficients, FP64
+  float* mi32;   // [3][cap]
+  float* hi32;   // [3][cap] H(m_init) at interior nodes
+  float* af32;   // [D][cap]
+  float* vA;     // [3][cap] v_hi at step n
+  float* vB;     // [3][cap] stage state v_hi + dt k1
+  float* vlo;    // [3][cap] carried rounding error of v
+  float* k1;     // [3][cap] stage-1 slope
+  float* V;      // [3][cap] sum_n w_n v_hi^n
+  float* Vc;     // [3][cap] Kahan compensation of V
+};
+
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+__host__ __device__ inline size_t fp32_slot_bytes(int D, size_t cap) {
+  return align256(3 * cap * 8) + align256(D * cap * 8) + 2 * align256(3 * cap * 4) +
+         align256(D * cap * 4) + 6 * align256(3 * cap * 4);
+}
+
+__device__ inline Fp32Slot carve_fp32(char* base, int D, size_t cap) {
+  Fp32Slot s;
+  char* p = base;
+  auto take = [&p](size_t bytes) { char* r = p; p += align256(bytes); return r; };
+  s.mi64 = reinterpret_cast<double*>(take(3 * cap * 8));
+  s.af64 = reinterpret_cast<double*>(take(D * cap * 8));
+  s.mi32 = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.hi32 = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.af32 = reinterpret_cast<float*>(take(D * cap * 4));
+  s.vA = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.vB = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.vlo = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.k1 = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.V = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.Vc = reinterpret_cast<float*>(take(3 * cap * 4));
+  return s;
+}
+
+// Spatial weight W(xi) at node idx (zero on and near the ring).
+template <int D, typename T>
+__device__ __forceinline__ T node_weight(const T* W1, int idx, int N) {
+  int j[3];
+  node_coords<D>(idx, N, j);
+  T W = W1[j[0]];
+  if (D > 1) W = W * W1[j[1]];
+  if (D > 2) W = W * W1[j[2]];
+  return W;
+}
+
+// H(W) at interior node idx in FP64 (the same staggered operator applied to W).
+template <int D, int R>
+__device__ __forceinline__ double stencil_of_weight(const double* W1, const double* af, size_t cap,
+                                                    const Strides<D>& st, int idx, int N, double cs) {
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int s = st.s[k];
+    auto Wn = [&](int o) { return node_weight<D, double>(W1, idx + o * s, N); };
+    const double* a = af + k * cap;
+    if (R == 1) {
+      acc += a[idx] * (Wn(1) - Wn(0)) - a[idx - s] * (Wn(0) - Wn(-1));
+    } else {
+      const double m_3 = Wn(-3), m_2 = Wn(-2), m_1 = Wn(-1), m0 = Wn(0), m1 = Wn(1), m2 = Wn(2), m3 = Wn(3);
+      const double g_2 = (m_3 - m0) + 27.0 * (m_1 - m_2);
+      const double g_1 = (m_2 - m1) + 27.0 * (m0 - m_1);
+      const double g0 = (m_1 - m2) + 27.0 * (m1 - m0);
+      const double g1 = (m0 - m3) + 27.0 * (m2 - m1);
+      acc += (a[idx - 2 * s] * g_2 - a[idx + s] * g1) + 27.0 * (a[idx] * g0 - a[idx - s] * g_1);
+    }
+  }
+  return acc * cs;
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
+  const int nmax = a.nmax;
+  extern __shared__ double smem[];
+  __shared__ int s_box;
+  const SetupSmem sm = carve_setup(smem, D, nmax, a.interp_k, a.n_terms);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t cap = (size_t)ipow<D>(nmax);
+  const Fp32Slot sl = carve_fp32(a.arena + (size_t)blockIdx.x * a.slot_bytes, D, cap);
+  const float am = (float)a.alpha_micro;
+
+  for (;;) {
+    const int b = next_box(a.queue, &s_box);
+    if (b >= a.n_boxes) break;
+    const BoxDesc bd = a.boxes[b];
+    const int N = bd.N;
+    const int ntot = ipow<D>(N);
+    const Strides<D> st(N);
+    box_setup_tables<D>(a, bd, sm);
+
+    // FP64 set-up: m_init = Q_[2k] (Section 4.1) and a^eps at the faces; zero state.
+    int bad = 0;
+    for (int idx = tid; idx < ntot; idx += nt) {
+      double P[3];
+      interp_P<D>(a, sm, N, idx, P);
+      const double inv = 1.0 / sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double mv = P[c] * inv;
+        const size_t o = c * cap + idx;
+        sl.mi64[o] = mv;
+        sl.mi32[o] = (float)mv;
+        sl.vA[o] = 0.f;
+        sl.vB[o] = 0.f;
+        sl.vlo[o] = 0.f;
+        sl.V[o] = 0.f;
+        sl.Vc[o] = 0.f;
+      }
+      int j[3];
+      node_coords<D>(idx, N, j);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        double v = 0.0;
+        if (j[k] < N - 1) {
+          v = face_coef<D>(a, sm, N, idx, k);
+          bad |= !(v > 0.0);
+        }
+        sl.af64[k * cap + idx] = v;
+        sl.af32[k * cap + idx] = (float)v;
+      }
+    }
+    if (bad) atomicOr(a.err, kErrCoefNonPositive);
+    __syncthreads();
+
+    const int nint = ipow<D>(N - 2 * R);
+    const double cs64 = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
+    const float cs = (float)cs64;
+    const double* W1d = a.W64 + bd.wofs;
+
+    // H(m_init) in FP64 (stored in FP32 for the loop); sum_xi W H(m_init) in FP64.
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int t = tid; t < nint; t += nt) {
+      const int idx = interior_node<D, R>(t, N);
+      double H[3];
+      stencil_H<D, R, double>(sl.mi64, sl.af64, cap, st, idx, cs64, H);
+      const double W = node_weight<D, double>(W1d, idx, N);
+      s0 += W * H[0];
+      s1 += W * H[1];
+      s2 += W * H[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sl.hi32[c * cap + idx] = (float)H[c];
+    }
+    double wsum = 0.0;
+    for (int n = 0; n <= a.msteps; ++n) wsum += a.w64[n];
+    s0 *= wsum;
+    s1 *= wsum;
+    s2 *= wsum;
+    __syncthreads();
+
+    const float dt = (float)bd.dt, hdt = 0.5f * (float)bd.dt;
+    for (int n = 0; n < a.msteps; ++n) {
+      const float wn = a.w32[n];
+      // Stage 1: k1 = f(m_init + v), v_B = v + dt k1, V += w_n v (Kahan).
+      for (int t = tid; t < nint; t += nt) {
+        const int idx = interior_node<D, R>(t, N);
+        float Hv[3];
+        stencil_H<D, R, float>(sl.vA, sl.af32, cap, st, idx, cs, Hv);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Hv[c] += sl.hi32[c * cap + idx];
+        float v[3], m[3], k1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          v[c] = sl.vA[c * cap + idx];
+          m[c] = sl.mi32[c * cap + idx] + v[c];
+        }
+        ll_rhs(m, Hv, am, k1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t o = c * cap + idx;
+          sl.k1[o] = k1[c];
+          sl.vB[o] = v[c] + dt * k1[c];
+          const float y = wn * v[c] - sl.Vc[o];
+          const float tV = sl.V[o] + y;
+          sl.Vc[o] = (tV - sl.V[o]) - y;
+          sl.V[o] = tV;
+        }
+      }
+      __syncthreads();
+      // Stage 2: k2 = f(m_init + v_B); the step's increment d = dt/2 (k1 + k2) plus
+      // the projection, added to v = v_hi + v_lo with an exact error term.
+      for (int t = tid; t < nint; t += nt) {
+        const int idx = interior_node<D, R>(t, N);
+        float Hv[3];
+        stencil_H<D, R, float>(sl.vB, sl.af32, cap, st, idx, cs, Hv);
+        float mi[3], m[3], k2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Hv[c] += sl.hi32[c * cap + idx];
+          mi[c] = sl.mi32[c * cap + idx];
+          m[c] = mi[c] + sl.vB[c * cap + idx];
+        }
+        ll_rhs(m, Hv, am, k2);
+        float vh[3], d[3], vt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          vh[c] = sl.vA[c * cap + idx];
+          d[c] = hdt * (sl.k1[c * cap + idx] + k2[c]);
+          vt[c] = vh[c] + d[c];
+        }
+        const float s = 2.f * (mi[0] * vt[0] + mi[1] * vt[1] + mi[2] * vt[2]) +
+                        (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+        const float r = rsqrtf(1.f + s);
+        const float cf = -s * r * r / (1.f + r);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t o = c * cap + idx;
+          const float inc = (d[c] + cf * (mi[c] + vt[c])) + sl.vlo[o];
+          const float nh = vh[c] + inc;
+          sl.vlo[o] = inc - (nh - vh[c]);
+          sl.vA[o] = nh;
+        }
+      }
+      __syncthreads();
+    }
+    // The final state's weight w_M (zero for K0 in K0^{p,q}) and the contraction with H(W).
+    const float wM = a.w32[a.msteps];
+    for (int t = tid; t < nint; t += nt) {
+      const int idx = interior_node<D, R>(t, N);
+      const double hw = stencil_of_weight<D, R>(W1d, sl.af64, cap, st, idx, N, cs64);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t o = c * cap + idx;
+        const double Vt = ((double)sl.V[o] - (double)sl.Vc[o]) + (double)wM * (double)sl.vA[o];
+        const double contrib = hw * Vt;
+        if (c == 0) s0 += contrib;
+        if (c == 1) s1 += contrib;
+        if (c == 2) s2 += contrib;
+      }
+    }
+    block_sum3(s0, s1, s2, sm.red);
+    if (tid == 0) {
+      a.Havg[bd.p] = s0;
+      a.Havg[a.P + bd.p] = s1;
+      a.Havg[2 * a.P + bd.p] = s2;
+      if (!(isfinite(s0) && isfinite(s1) && isfinite(s2))) atomicOr(a.err, kErrNonFinite);
+    }
+  }
+}
+
+template <int D, int R>
+static cudaError_t launch_t(const MicroArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  micro_fp32_kernel<D, R><<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int R>
+static cudaError_t prepare_t(int block, size_t smem, int* per_sm) {
+  auto kern = micro_fp32_kernel<D, R>;
+  // Raise the kernel's limit to the device's opt-in maximum once, so that
+  // handles with different table sizes never lower it for each other.
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
+}
+
+#define HMM_DISPATCH(FN, ...)                                      \
+  do {                                                              \
+    if (radius == 3) {                                             \
+      if (dim == 1) return FN<1, 3>(__VA_ARGS__);                  \
+      if (dim == 2) return FN<2, 3>(__VA_ARGS__);                  \
+      if (dim == 3) return FN<3, 3>(__VA_ARGS__);                  \
+    } else if (radius == 1) {                                     \
+      if (dim == 1) return FN<1, 1>(__VA_ARGS__);                  \
+      if (dim == 2) return FN<2, 1>(__VA_ARGS__);                  \
+      if (dim == 3) return FN<3, 1>(__VA_ARGS__);                  \
+    }                                                              \
+    return cudaErrorInvalidValue;                                  \
+  } while (0)
+
+cudaError_t launch_micro_fp32(const MicroArgs& a, int dim, int radius, int grid, int block,
+                              size_t smem, cudaStream_t st) {
+  HMM_DISPATCH(launch_t, a, grid, block, smem, st);
+}
+
+cudaError_t prepare_micro_fp32(int dim, int radius, int block, size_t smem, int* ctas_per_sm) {
+  HMM_DISPATCH(prepare_t, block, smem, ctas_per_sm);
+}
+
+size_t micro_slot_bytes_fp32(int dim, int nmax) {
+  size_t cap = 1;
+  for (int i = 0; i < dim; ++i) cap *= (size_t)nmax;
+  return align256(fp32_slot_bytes(dim, cap));
+}
+
+}  // namespace hmm

@@ -1,0 +1,231 @@
+// Plain FP64 micro-batch kernel: the micro problem (eq. micro) of every macro
+// point, stepped by HeunP (Section 3.1) with the Dirichlet ring (Section 4.2),
+// and reduced by the kernel-weighted average (Section 2.3, eq. upscaling), all
+// in FP64 arithmetic. One CTA per box, boxes pulled from an atomic queue.
+//
+// The state is carried as v = m - m_init. Since H is linear, H(m) = H(m_init) +
+// H(v) and the scheme is unchanged; what changes is the rounding: increments of
+// size dt |f| are added to |v| ~ eps |grad m| instead of to |m| = 1, so the
+// FP64 rounding floor of H_avg drops from ~1e-12 (the m-form) to ~1e-15.
+// The projection m^{n+1} = m~/|m~| becomes v^{n+1} = v~ + c (m_init + v~) with
+// s = |m_init + v~|^2 - 1 and c = -s / (sqrt(1+s) (1 + sqrt(1+s))).
+#include "micro_common.cuh"
+#include "stencil.cuh"
+
+namespace hmm {
+
+template <int D, int R>
+__global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
+  const int nmax = a.nmax;
+  extern __shared__ double smem[];
+  __shared__ int s_box;
+  const SetupSmem sm = carve_setup(smem, D, nmax, a.interp_k, a.n_terms);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t cap = (size_t)ipow<D>(nmax);
+  double* mi = reinterpret_cast<double*>(a.arena + (size_t)blockIdx.x * a.slot_bytes);
+  double* hi = mi + 3 * cap;  // H(m_init)
+  double* vA = hi + 3 * cap;
+  double* vB = vA + 3 * cap;
+  double* q = vB + 3 * cap;
+  double* af = q + 3 * cap;
+
+  for (;;) {
+    const int b = next_box(a.queue, &s_box);
+    if (b >= a.n_boxes) break;
+    const BoxDesc bd = a.boxes[b];
+    const int N = bd.N;
+    const int ntot = ipow<D>(N);
+    const Strides<D> st(N);
+    box_setup_tables<D>(a, bd, sm);
+
+    // Initial data Q_[2k] at every node (Section 4.1), a^eps at every face, v = 0.
+    int bad = 0;
+    for (int idx = tid; idx < ntot; idx += nt) {
+      double P[3];
+      interp_P<D>(a, sm, N, idx, P);
+      const double inv = 1.0 / sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        mi[c * cap + idx] = P[c] * inv;
+        vA[c * cap + idx] = 0.0;
+        vB[c * cap + idx] = 0.0;
+      }
+      int j[3];
+      node_coords<D>(idx, N, j);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        double v = 0.0;
+        if (j[k] < N - 1) {
+          v = face_coef<D>(a, sm, N, idx, k);
+          bad |= !(v > 0.0);
+        }
+        af[k * cap + idx] = v;
+      }
+    }
+    if (bad) atomicOr(a.err, kErrCoefNonPositive);
+    __syncthreads();
+
+    const double dt = bd.dt, hdt = 0.5 * bd.dt;
+    const double cs = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
+    const double* W1 = a.W64 + bd.wofs;
+    const int nint = ipow<D>(N - 2 * R);
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+
+    // H(m_init) and its weighted sum (times sum_n w_n).
+    {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      for (int t = tid; t < nint; t += nt) {
+        const int idx = interior_node<D, R>(t, N);
+        double H[3];
+        stencil_H<D, R, double>(mi, af, cap, st, idx, cs, H);
+        int j[3];
+        node_coords<D>(idx, N, j);
+        double W = W1[j[0]];
+        if (D > 1) W = W * W1[j[1]];
+        if (D > 2) W = W * W1[j[2]];
+        s0 += W * H[0];
+        s1 += W * H[1];
+        s2 += W * H[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hi[c * cap + idx] = H[c];
+      }
+      double wsum = 0.0;
+      for (int n = 0; n <= a.msteps; ++n) wsum += a.w64[n];
+      acc0 = s0 * wsum;
+      acc1 = s1 * wsum;
+      acc2 = s2 * wsum;
+    }
+    __syncthreads();
+
+    for (int n = 0; n <= a.msteps; ++n) {
+      const double wn = a.w64[n];
+      if (n == a.msteps && wn == 0.0) break;  // K0(1) = 0: no final stencil pass
+      // Stage 1: H(m^n) = H(m_init) + H(v^n), its weighted sum, k1, v + dt k1, v + dt/2 k1.
+      for (int t = tid; t < nint; t += nt) {
+        const int idx = interior_node<D, R>(t, N);
+        double Hv[3];
+        stencil_H<D, R, double>(vA, af, cap, st, idx, cs, Hv);
+        if (wn != 0.0) {
+          int j[3];
+          node_coords<D>(idx, N, j);
+          double W = W1[j[0]];
+          if (D > 1) W = W * W1[j[1]];
+          if (D > 2) W = W * W1[j[2]];
+          const double ww = wn * W;
+          acc0 += ww * Hv[0];
+          acc1 += ww * Hv[1];
+          acc2 += ww * Hv[2];
+        }
+        if (n == a.msteps) continue;
+        double v[3], m[3], H[3], k1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          v[c] = vA[c * cap + idx];
+          m[c] = mi[c * cap + idx] + v[c];
+          H[c] = hi[c * cap + idx] + Hv[c];
+        }
+        ll_rhs(m, H, a.alpha_micro, k1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          q[c * cap + idx] = v[c] + hdt * k1[c];
+          vB[c * cap + idx] = v[c] + dt * k1[c];
+        }
+      }
+      if (n == a.msteps) break;
+      __syncthreads();
+      // Stage 2: k2 = f(m + dt k1), m^{n+1} = normalise(m + dt/2 (k1 + k2)), as v.
+      for (int t = tid; t < nint; t += nt) {
+        const int idx = interior_node<D, R>(t, N);
+        double Hv[3];
+        stencil_H<D, R, double>(vB, af, cap, st, idx, cs, Hv);
+        double mv[3], m[3], H[3], k2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          mv[c] = mi[c * cap + idx];
+          m[c] = mv[c] + vB[c * cap + idx];
+          H[c] = hi[c * cap + idx] + Hv[c];
+        }
+        ll_rhs(m, H, a.alpha_micro, k2);
+        double vt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vt[c] = q[c * cap + idx] + hdt * k2[c];
+        const double s = 2.0 * (mv[0] * vt[0] + mv[1] * vt[1] + mv[2] * vt[2]) +
+                         (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) +
+                         ((mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2]) - 1.0);
+        const double rt = sqrt(1.0 + s);
+        const double cf = -s / (rt * (1.0 + rt));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vA[c * cap + idx] = vt[c] + cf * (mv[c] + vt[c]);
+      }
+      __syncthreads();
+    }
+    block_sum3(acc0, acc1, acc2, sm.red);
+    if (tid == 0) {
+      a.Havg[bd.p] = acc0;
+      a.Havg[a.P + bd.p] = acc1;
+      a.Havg[2 * a.P + bd.p] = acc2;
+      if (!(isfinite(acc0) && isfinite(acc1) && isfinite(acc2))) atomicOr(a.err, kErrNonFinite);
+    }
+  }
+}
+
+template <int D, int R>
+static cudaError_t launch_t(const MicroArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  micro_fp64_kernel<D, R><<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int R>
+static cudaError_t prepare_t(int block, size_t smem, int* per_sm) {
+  auto kern = micro_fp64_kernel<D, R>;
+  // Raise the kernel's limit to the device's opt-in maximum once, so that
+  // handles with different table sizes never lower it for each other.
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
+}
+
+#define HMM_DISPATCH(FN, ...)                                      \
+  do {                                                              \
+    if (radius == 3) {                                             \
+      if (dim == 1) return FN<1, 3>(__VA_ARGS__);                  \
+      if (dim == 2) return FN<2, 3>(__VA_ARGS__);                  \
+      if (dim == 3) return FN<3, 3>(__VA_ARGS__);                  \
+    } else if (radius == 1) {                                     \
+      if (dim == 1) return FN<1, 1>(__VA_ARGS__);                  \
+      if (dim == 2) return FN<2, 1>(__VA_ARGS__);                  \
+      if (dim == 3) return FN<3, 1>(__VA_ARGS__);                  \
+    }                                                              \
+    return cudaErrorInvalidValue;                                  \
+  } while (0)
+
+cudaError_t launch_micro_fp64(const MicroArgs& a, int dim, int radius, int grid, int block,
+                              size_t smem, cudaStream_t st) {
+  HMM_DISPATCH(launch_t, a, grid, block, smem, st);
+}
+
+cudaError_t prepare_micro_fp64(int dim, int radius, int block, size_t smem, int* ctas_per_sm) {
+  HMM_DISPATCH(prepare_t, block, smem, ctas_per_sm);
+}
+
+size_t micro_smem_bytes(int dim, int nmax, int interp_k, int n_terms) {
+  return sizeof(double) * setup_smem_doubles(dim, nmax, interp_k, n_terms);
+}
+
+size_t micro_slot_bytes_fp64(int dim, int nmax) {
+  size_t cap = 1;
+  for (int i = 0; i < dim; ++i) cap *= (size_t)nmax;
+  size_t b = (size_t)(5 * 3 + dim) * cap * sizeof(double);
+  return (b + 255) & ~(size_t)255;
+}
+
+}  // namespace hmm

@@ -1,0 +1,95 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point that
+include/hmm.h declares, and rejects invalid parameters on the host (no GPU
+needed: validation happens before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_09463_gb300 import build, load_library
+    build()
+    return load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hmm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2108_09463_gb300 import EXPORTED
+    decl = _declared()
+    assert decl == sorted(EXPORTED)
+    for name in decl:
+        assert hasattr(lib, name), name
+
+
+def _struct_fields(src, name):
+    body = re.search(r"typedef struct \{([^{}]*)\} " + name + ";", src).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.replace("const", " ").replace("*", " ").strip()
+        if not decl:
+            continue
+        # drop the type (first token), keep the declarators
+        decl = decl.split(None, 1)[1]
+        out += [re.sub(r"\[\d+\]", "", v).strip() for v in decl.split(",")]
+    return out
+
+
+def test_struct_layout_matches_header():
+    """The ctypes mirror has the field order of hmm_params / hmm_coef_term."""
+    from paper_2108_09463_gb300._lib import HmmCoefTerm, HmmParams
+    src = open(os.path.join(ROOT, "include", "hmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    assert [f[0] for f in HmmParams._fields_] == _struct_fields(src, "hmm_params")
+    assert [f[0] for f in HmmCoefTerm._fields_] == _struct_fields(src, "hmm_coef_term")
+
+
+def _init(lib, cfg, **over):
+    from paper_2108_09463_gb300._lib import make_params
+    p, keep = make_params(cfg)
+    for k, v in over.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    st = lib.hmm_init(ctypes.byref(p), None, ctypes.byref(h))
+    msg = lib.hmm_last_error(None).decode()
+    if st == 0:
+        lib.hmm_destroy(h)
+    return st, msg
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(dim=4), "dim"), (dict(alpha=0.0), "alpha"), (dict(alpha=1.5), "alpha"),
+    (dict(alpha_micro=-1.0), "alpha_micro"), (dict(stencil_order=3), "stencil_order"),
+    (dict(interp_order=6), "interp_order"), (dict(precision=5), "precision"),
+    (dict(micro_steps=0), "micro_steps"), (dict(box_n=5), "box_n"), (dict(box_n=300), "box_n"),
+    (dict(eps=-1.0), "eps"), (dict(pts_per_eps=0.0), "pts_per_eps"), (dict(n_terms=9), "n_terms"),
+])
+def test_invalid_params_rejected_on_host(lib, over, needle):
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=10)
+    st, msg = _init(lib, cfg, **over)
+    assert st == 1, (st, msg)
+    assert needle in msg
+
+
+def test_averaging_box_must_avoid_ring(lib):
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=20, micro_steps=10)  # mu = 0.8 mu' reaches the ring
+    st, msg = _init(lib, cfg)
+    assert st == 1 and "ring" in msg
+
+
+def test_null_arguments(lib):
+    assert lib.hmm_init(None, None, None) == 1
+    assert lib.hmm_micro_batch(None, None, None) == 7
+    assert lib.hmm_macro_step(None, None, 1) == 7
+    lib.hmm_destroy(None)

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Error measure: rel = max_i |H_gpu,i - H_ref,i|_2 / max_i |H_ref,i|_2 over macro
+points i. Bounds: 1e-12 for the FP64 method, 1e-6 for the batched FP32 form
+(the accuracy targets stated for the two forms).
+
+The FP64 method is compared with the oracle evaluated in long double: the
+oracle's own FP64 rounding floor for H_avg is 1-3e-12 relative (measured in
+tests/test_oracle_precision.py), above the 1e-12 bar, so a long-double
+evaluation of the same scheme is the reference that can resolve it. The FP32
+form is compared with the FP64 oracle.
+
+Small cases run the oracle on every box; full-size workloads run the GPU on the
+whole batch (the launch configuration the benchmark times) and the oracle on a
+sample of boxes, including the largest and smallest boxes of uneven batches.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hmm_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-6}
+ORACLE_FP64_FLOOR = 3e-12      # bound on the FP64 oracle's own rounding error (relative)
+N_LD_POINTS = 6                # boxes evaluated by the long-double oracle per case
+
+
+def reference(cfg, M0, precision, points=None):
+    """Oracle H_avg at ``points`` (FP64 oracle for the FP32 form, long double for FP64)."""
+    if precision == 0:
+        if points is None:
+            P = cfg.n_points
+            points = sorted(set([0, P - 1] + list(range(0, P, max(1, P // (N_LD_POINTS - 2))))))[:N_LD_POINTS]
+        H = O.micro_batch(cfg, M0, points=points, dtype=np.longdouble)
+        return points, H
+    return points, O.micro_batch(cfg, M0, points=points)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_09463_gb300 import build
+    build()
+    return torch
+
+
+def rel_err(Hg, Hr):
+    d = (np.asarray(Hg, dtype=Hr.dtype) - Hr).astype(np.float64)
+    return np.linalg.norm(d, axis=0).max() / np.linalg.norm(Hr.astype(np.float64), axis=0).max()
+
+
+def gpu_micro(torch, cfg, M0, precision):
+    from paper_2108_09463_gb300 import HMM
+    h = HMM(cfg, precision=precision)
+    M = torch.from_numpy(M0).cuda()
+    H = h.micro_batch(M).cpu().numpy()
+    info = h.box_info()
+    h.close()
+    return H, info
+
+
+SMALL = {
+    "c1_full": ("c1_1d", {}),
+    "1d_order2_interp2": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=120,
+                                        stencil_order=2, interp_order=2)),
+    "2d_small": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=60)),
+    "2d_ragged": ("c2_2d", dict(n_macro=(6, 7, 1), box_n=37, micro_steps=33)),
+    "2d_order2": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=50, stencil_order=2)),
+    "3d_small": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=16, mu_over_eps=0.9, micro_steps=30)),
+    "2d_slow_fast": ("c3_2d_uneven", dict(n_macro=(8, 8, 1), eps_field=None, box_n_field=None,
+                                          eps=1 / 250, box_n=32, micro_steps=40)),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(SMALL))
+def test_small_parity(torch_cuda, case, precision):
+    name, over = SMALL[case]
+    cfg = W.config(name, **over)
+    if name == "c3_2d_uneven":
+        cfg = cfg.replace(eps_field=None, box_n_field=None)
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, precision)
+    pts, Hr = reference(cfg, M0, precision)
+    e = rel_err(Hg if pts is None else Hg[:, pts], Hr)
+    assert e < TOL[precision], (case, precision, e)
+    # the library's per-box geometry equals the oracle's
+    for p in (0, cfg.n_points - 1):
+        geo = O.box_geometry(cfg, p)
+        assert info["N"][p] == geo["N"]
+        assert abs(info["dt"][p] / geo["dt"] - 1) < 1e-14
+        assert abs(info["mu"][p] / geo["mu"] - 1) < 1e-14
+
+
+def _uneven_small():
+    cfg = W.config("c3_2d_uneven", n_macro=(12, 12, 1), micro_steps=40, eps_field=None, box_n_field=None)
+    eps, n = W.uneven_eps_and_n(cfg, K=8.0, mu_prime=0.0075, nmin=24, nmax=48, step=8)
+    return cfg.replace(eps_field=eps, box_n_field=n)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_uneven_boxes_parity(torch_cuda, precision):
+    cfg = _uneven_small()
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, precision)
+    N = info["N"]
+    assert N.min() == 24 and N.max() == 48
+    nsample = 4 if precision == 0 else 14
+    pts = sorted(set([int(np.argmin(N)), int(np.argmax(N))] +
+                     list(np.random.default_rng(0).choice(cfg.n_points, nsample, replace=False))))
+    _, Hr = reference(cfg, M0, precision, pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[precision]
+
+
+FULL = [("c2_2d", 0), ("c2_2d", 1), ("c3_2d_uneven", 1)]
+
+
+@pytest.mark.parametrize("name,precision", FULL)
+def test_full_size_sampled(torch_cuda, name, precision):
+    cfg = W.config(name)
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, precision)
+    assert np.all(np.isfinite(Hg))
+    N = info["N"]
+    rng = np.random.default_rng(1)
+    if precision == 0:
+        pts = [0, int(rng.integers(cfg.n_points))]
+    else:
+        pts = sorted(set([0, cfg.n_points - 1, int(np.argmax(N)), int(np.argmin(N))] +
+                         list(rng.choice(cfg.n_points, 2, replace=False))))
+    _, Hr = reference(cfg, M0, precision, pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[precision], name
+
+
+MACRO = {
+    "1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=100), 5),
+    "2d": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30), 4),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(MACRO))
+def test_macro_steps_parity(torch_cuda, case, precision):
+    from paper_2108_09463_gb300 import HMM
+    name, over, nsteps = MACRO[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    h = HMM(cfg, precision=precision)
+    M = torch_cuda.from_numpy(M0).cuda()
+    h.macro_step(M, nsteps)
+    Mg = M.cpu().numpy()
+    st = O.MacroStepper(cfg, M0, dt=h.macro_dt())
+    assert abs(h.macro_dt() / O.macro_dt(cfg) - 1) < 1e-14
+    hmax = np.linalg.norm(st.havg(M0), axis=0).max()
+    for _ in range(nsteps):
+        st.step()
+    err = np.abs(Mg - st.M).max()
+    # each macro step moves M by dt * O(|H_avg|) through at most 4 stages, so an
+    # H_avg error within TOL (relative to max |H_avg|) bounds the M error by the
+    # expression below; the FP64 oracle adds its own rounding floor.
+    tol = TOL[precision] + (ORACLE_FP64_FLOOR if precision == 0 else 0.0)
+    bound = 4 * nsteps * h.macro_dt() * tol * hmax + 1e-14
+    assert err < bound, (err, bound)
+    assert np.abs(np.linalg.norm(Mg, axis=0) - 1).max() < 1e-13
+    h.close()
+
+
+def test_restart_is_bit_identical(torch_cuda):
+    from paper_2108_09463_gb300 import HMM
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=20)
+    M0 = torch_cuda.from_numpy(W.initial_field(cfg)).cuda()
+    a = HMM(cfg, precision=1)
+    Ma = M0.clone()
+    a.macro_step(Ma, 10)
+    b = HMM(cfg, precision=1)
+    Mb = M0.clone()
+    b.macro_step(Mb, 6)
+    hist, j = b.get_state()
+    Msave = Mb.clone()
+    b.close()
+    c = HMM(cfg, precision=1)
+    c.set_state(hist, j)
+    c.macro_step(Msave, 4)
+    assert torch_cuda.equal(Ma, Msave)
+    a.close()
+    c.close()
+
+
+def test_graph_replay_equals_single_steps(torch_cuda):
+    from paper_2108_09463_gb300 import HMM
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=20)
+    M0 = torch_cuda.from_numpy(W.initial_field(cfg)).cuda()
+    a, b = HMM(cfg, precision=1), HMM(cfg, precision=1)
+    Ma, Mb = M0.clone(), M0.clone()
+    a.macro_step(Ma, 5)
+    for _ in range(5):
+        b.macro_step(Mb, 1)
+    assert torch_cuda.equal(Ma, Mb)
+
+
+def test_host_entry_points(torch_cuda):
+    from paper_2108_09463_gb300 import HMM
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=20)
+    M0 = W.initial_field(cfg)
+    h = HMM(cfg, precision=1)
+    Hd = h.micro_batch(torch_cuda.from_numpy(M0).cuda()).cpu().numpy()
+    Hh = np.empty_like(M0)
+    h.micro_batch_host(np.ascontiguousarray(M0), Hh)
+    assert np.array_equal(Hd, Hh)
+    Md = torch_cuda.from_numpy(M0).cuda()
+    h2 = HMM(cfg, precision=1)
+    h2.macro_step(Md, 3)
+    Mh = M0.copy()
+    h.macro_step_host(Mh, 3)
+    assert np.array_equal(Md.cpu().numpy(), Mh)
+
+
+def test_nonfinite_input_reported(torch_cuda):
+    from paper_2108_09463_gb300 import HMM, HmmError
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=10)
+    M0 = W.initial_field(cfg)
+    M0[:, 9] = np.nan
+    h = HMM(cfg, precision=1)
+    with pytest.raises(HmmError) as ei:
+        h.micro_batch(torch_cuda.from_numpy(M0).cuda())
+    assert ei.value.status == 6
+    # the handle stays usable after the error
+    M1 = W.initial_field(cfg)
+    H = h.micro_batch(torch_cuda.from_numpy(M1).cuda())
+    assert torch_cuda.isfinite(H).all()
