@@ -150,6 +150,39 @@ hmm_status hmm_box_info(void* handle, double* dt, double* mu, double* dx, int* n
 /* The macro time step the handle uses. */
 hmm_status hmm_macro_dt(void* handle, double* dt_macro);
 
+/* Allocation-free variant of hmm_micro_batch. This entry point is an addition of
+ * this library; the paper has no counterpart.
+ *
+ * It is for callers that must not allocate device memory: code that runs inside
+ * a memory allocator's own callbacks (where cudaMalloc would re-enter the
+ * allocator), applications whose device memory is fully reserved up front by
+ * another framework's memory pool (so cudaMalloc fails), and latency-critical
+ * paths that cannot afford cudaMalloc/cudaFree, which may synchronise the device.
+ * It takes the problem directly (no handle), runs the same batched FP32 micro
+ * solve as hmm_micro_batch with kernel_variant 0/1, and calls no cudaMalloc,
+ * cudaFree or other allocating routine: every buffer it needs (box table,
+ * weight tables, work counter, error word, per-CTA arenas) is carved out of one
+ * fixed device array of 32 MiB inside the library, reserved on every GPU that
+ * loads the library and held until the process exits.
+ *
+ * Limits: precision must be HMM_FP32_BATCHED; eps_field and box_n_field must be
+ * NULL (uniform boxes); micro_steps <= 16384; the box table, weight tables and
+ * at least one box's arena must fit in the 32 MiB (else HMM_ERR_INVALID_ARG with
+ * the sizes in hmm_last_error(NULL)). Fewer CTAs run than with hmm_init when the
+ * arenas of a full grid do not fit, so large batches run slower.
+ * M_dev, Havg_dev: SoA 3 x P FP64 device buffers as for hmm_micro_batch;
+ * cuda_stream: the stream to run on (NULL = legacy default stream); the call
+ * synchronises it before returning. Errors are reported through
+ * hmm_last_error(NULL).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once for that device; make that first call before
+ * any stream capture begins. All calls share the one array and each call
+ * overwrites it: calls that overlap on the GPU (other threads, other streams)
+ * race and must be serialised by the caller. */
+hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const double* M_dev, double* Havg_dev,
+                                   void* cuda_stream);
+
 /* One-line description of the last failure on this handle ("" if none). Valid
  * until the next call on the handle. NULL handle: the last hmm_init failure. */
 const char* hmm_last_error(void* handle);

@@ -22,7 +22,8 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 # The symbols include/hmm.h declares (checked by the CPU test suite).
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
             "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
-            "hmm_box_info", "hmm_macro_dt", "hmm_last_error", "hmm_destroy")
+            "hmm_box_info", "hmm_macro_dt", "hmm_micro_batch_noalloc", "hmm_last_error",
+            "hmm_destroy")
 
 
 class HmmCoefTerm(ctypes.Structure):
@@ -69,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_stats.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
     lib.hmm_box_info.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.hmm_macro_dt.argtypes = [c_void_p, POINTER(c_double)]
+    lib.hmm_micro_batch_noalloc.argtypes = [POINTER(HmmParams), c_void_p, c_void_p, c_void_p]
     lib.hmm_last_error.argtypes = [c_void_p]
     lib.hmm_last_error.restype = c_char_p
     lib.hmm_destroy.argtypes = [c_void_p]
@@ -223,3 +225,24 @@ class HMM:
             self.close()
         except Exception:
             pass
+
+
+def micro_batch_noalloc(cfg, M, out, stream=None):
+    """hmm_micro_batch_noalloc: the FP32 micro batch without any device allocation.
+
+    For callers that cannot allocate device memory (see include/hmm.h): all
+    working memory comes from a fixed 32 MiB array inside the library. M and
+    out are contiguous float64 CUDA tensors of shape (3, P); ``cfg`` describes a
+    batch of uniform boxes. Raises HmmError on failure.
+    """
+    import torch
+    lib = load_library()
+    params, keep = make_params(cfg, precision=HMM_FP32_BATCHED)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = lib.hmm_micro_batch_noalloc(ctypes.byref(params), c_void_p(M.data_ptr()),
+                                     c_void_p(out.data_ptr()), c_void_p(stream.cuda_stream))
+    del keep
+    if st != HMM_OK:
+        raise HmmError(st, lib.hmm_last_error(None).decode())
+    return out

@@ -25,7 +25,7 @@ using namespace hmm;
 
 namespace {
 
-thread_local std::string g_init_error;
+thread_local char g_init_error[512] = "";   // last failure of a call without a handle
 
 // ---------------------------------------------------------------- rationals
 struct Rat {
@@ -123,10 +123,16 @@ bool moment_one_sided(int q, int n, Rat* r) {
   return true;
 }
 
-// Solve sum_k c_k mom(k + r) = delta_{r0}, r = 0..p, in exact rationals.
-bool solve_kernel(int p, int q, bool one_sided, std::vector<double>* out) {
+}  // namespace
+
+namespace hmm {
+namespace host {
+
+// Solve sum_k c_k mom(k + r) = delta_{r0}, r = 0..p, in exact rationals (p <= kMaxKernelP).
+bool kernel_coeffs(int p, int q, bool one_sided, double* out) {
+  if (p < 0 || p > kMaxKernelP) return false;
   const int n = p + 1;
-  std::vector<std::vector<Rat>> A(n, std::vector<Rat>(n + 1));
+  Rat A[kMaxKernelP + 1][kMaxKernelP + 2];
   for (int r = 0; r < n; ++r) {
     for (int k = 0; k < n; ++k) {
       bool ok = one_sided ? moment_one_sided(q, k + r, &A[r][k]) : moment_two_sided(q, k + r, &A[r][k]);
@@ -139,7 +145,8 @@ bool solve_kernel(int p, int q, bool one_sided, std::vector<double>* out) {
     for (int r = col; r < n; ++r)
       if (A[r][col].n != 0) { piv = r; break; }
     if (piv < 0) return false;
-    std::swap(A[col], A[piv]);
+    if (piv != col)
+      for (int c = 0; c <= n; ++c) std::swap(A[col][c], A[piv][c]);
     for (int r = 0; r < n; ++r) {
       if (r == col || A[r][col].n == 0) continue;
       Rat fac;
@@ -152,26 +159,25 @@ bool solve_kernel(int p, int q, bool one_sided, std::vector<double>* out) {
       }
     }
   }
-  out->resize(n);
   for (int i = 0; i < n; ++i) {
     Rat c;
     if (!rat_div(A[i][n], A[i][i], &c)) return false;
-    (*out)[i] = (double)rat_ld(c);
+    out[i] = (double)rat_ld(c);
   }
   return true;
 }
 
-double eval_kernel(const std::vector<double>& c, int q, double x) {  // K, support (-1, 1)
+double eval_kernel(const double* c, int p, int q, double x) {  // K, support (-1, 1)
   if (!(std::fabs(x) < 1.0)) return 0.0;
   double poly = 0.0;
-  for (int k = (int)c.size() - 1; k >= 0; --k) poly = poly * x + c[k];
+  for (int k = p; k >= 0; --k) poly = poly * x + c[k];
   return std::pow(1.0 - x * x, q + 1) * poly;
 }
 
-double eval_kernel0(const std::vector<double>& c, int q, double t) {  // K0, support (0, 1)
+double eval_kernel0(const double* c, int p, int q, double t) {  // K0, support (0, 1)
   if (!(t > 0.0 && t < 1.0)) return 0.0;
   double poly = 0.0;
-  for (int k = (int)c.size() - 1; k >= 0; --k) poly = poly * t + c[k];
+  for (int k = p; k >= 0; --k) poly = poly * t + c[k];
   return std::pow(t * (1.0 - t), q + 1) * poly;
 }
 
@@ -194,6 +200,23 @@ double heun_limit(double a) {
   }
   return lo;
 }
+
+double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order,
+                double dx) {
+  const double lam = stencil_order == 2 ? 4.0 : (28.0 / 12.0) * (28.0 / 12.0);
+  const double omega = a_max * dim * lam / (dx * dx);
+  return dt_safety * heun_limit(alpha_micro) / omega;
+}
+
+}  // namespace host
+
+void set_null_handle_error(const char* msg) {
+  std::snprintf(g_init_error, sizeof g_init_error, "%s", msg);
+}
+
+}  // namespace hmm
+
+namespace {
 
 constexpr double kMacroDtConstant = 0.06;
 
@@ -252,7 +275,7 @@ struct HmmHandle {
 namespace {
 
 hmm_status fail(HmmHandle* h, hmm_status s, const std::string& msg) {
-  if (h) h->err = msg; else g_init_error = msg;
+  if (h) h->err = msg; else hmm::set_null_handle_error(msg.c_str());
   return s;
 }
 
@@ -344,21 +367,20 @@ hmm_status build(HmmHandle* h) {
   if (!(h->a_max > 0)) return fail(h, HMM_ERR_INVALID_ARG, "coefficient upper bound must be positive");
 
   // Smoothing kernels (exact rationals).
-  std::vector<double> cK, cK0;
-  if (!solve_kernel(p.px, p.qx, false, &cK) || !solve_kernel(p.pt, p.qt, true, &cK0))
+  double cK[host::kMaxKernelP + 1], cK0[host::kMaxKernelP + 1];
+  if (!host::kernel_coeffs(p.px, p.qx, false, cK) || !host::kernel_coeffs(p.pt, p.qt, true, cK0))
     return fail(h, HMM_ERR_INVALID_ARG, "kernel moment system overflowed 128-bit rationals");
 
   // Time weights w_n = K0(n/M), normalised to sum 1.
   const int M = p.micro_steps;
   std::vector<double> w(M + 1);
   double ws = 0;
-  for (int n = 0; n <= M; ++n) ws += (w[n] = eval_kernel0(cK0, p.qt, (double)n / (double)M));
+  for (int n = 0; n <= M; ++n) ws += (w[n] = host::eval_kernel0(cK0, p.pt, p.qt, (double)n / (double)M));
   if (!(ws != 0)) return fail(h, HMM_ERR_INVALID_ARG, "time weights vanish");
   for (auto& v : w) v /= ws;
 
   // Boxes.
-  const double smax = heun_limit(p.alpha_micro);
-  const double lam = p.stencil_order == 2 ? 4.0 : (28.0 / 12.0) * (28.0 / 12.0);
+
   const int nlim = max_n_for_dim(h->dim);
   std::map<int, int> class_ofs;
   std::vector<double> W64;
@@ -386,8 +408,7 @@ hmm_status build(HmmHandle* h) {
     bd.dx = bd.eps / p.pts_per_eps;
     const double mup = (bd.N - 1) * bd.dx / 2.0;
     const double mu = p.mu_over_eps > 0 ? p.mu_over_eps * bd.eps : 0.8 * mup;
-    const double omega = h->a_max * h->dim * lam / (bd.dx * bd.dx);
-    bd.dt = p.dt_safety * smax / omega;
+    bd.dt = host::micro_dt(p.dt_safety, p.alpha_micro, h->a_max, h->dim, p.stencil_order, bd.dx);
     if (!(bd.dt > 0)) return fail(h, HMM_ERR_INVALID_ARG, "micro time step is not positive");
     auto it = class_ofs.find(bd.N);
     if (it == class_ofs.end()) {
@@ -396,7 +417,7 @@ hmm_status build(HmmHandle* h) {
       double s = 0;
       for (int jn = 0; jn < bd.N; ++jn) {
         const double xi = (jn - (bd.N - 1) / 2.0) * bd.dx;
-        const double v = eval_kernel(cK, p.qx, xi / mu);
+        const double v = host::eval_kernel(cK, p.px, p.qx, xi / mu);
         W64.push_back(v);
         s += v;
       }
@@ -619,7 +640,7 @@ hmm_status end_call(HmmHandle* h) {
 extern "C" {
 
 hmm_status hmm_init(const hmm_params* params, void* cuda_stream, void** handle_out) {
-  g_init_error.clear();
+  g_init_error[0] = 0;
   if (!params || !handle_out) return fail(nullptr, HMM_ERR_INVALID_ARG, "null params or handle_out");
   *handle_out = nullptr;
   HmmHandle* h = new (std::nothrow) HmmHandle();
@@ -628,7 +649,7 @@ hmm_status hmm_init(const hmm_params* params, void* cuda_stream, void** handle_o
   h->user_stream = static_cast<cudaStream_t>(cuda_stream);
   hmm_status s = build(h);
   if (s != HMM_OK) {
-    g_init_error = h->err;
+    hmm::set_null_handle_error(h->err.c_str());
     free_all(h);
     delete h;
     return s;
@@ -765,7 +786,7 @@ hmm_status hmm_macro_dt(void* handle, double* dt_macro) {
 
 const char* hmm_last_error(void* handle) {
   HmmHandle* h = as_handle(handle);
-  return h ? h->err.c_str() : g_init_error.c_str();
+  return h ? h->err.c_str() : g_init_error;
 }
 
 void hmm_destroy(void* handle) {

@@ -91,4 +91,18 @@ cudaError_t launch_rk4_stage(const double* M, const double* Ms, const double* H,
                              int P, cudaStream_t st);
 cudaError_t launch_check_finite(const double* x, int n, int* err, cudaStream_t st);
 
+// Message returned by hmm_last_error(NULL) (copied into a fixed buffer).
+void set_null_handle_error(const char* msg);
+
+// Host-side set-up shared by hmm_init and the allocation-free entry point.
+namespace host {
+constexpr int kMaxKernelP = 6;
+bool kernel_coeffs(int p, int q, bool one_sided, double* out);   // out[p + 1]
+double eval_kernel(const double* c, int p, int q, double x);
+double eval_kernel0(const double* c, int p, int q, double t);
+double heun_limit(double alpha);
+double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order,
+                double dx);
+}  // namespace host
+
 }  // namespace hmm
