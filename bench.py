@@ -212,7 +212,7 @@ def run_ours(args, rank, world, local_rank):
     hbm = peaks.get("hbm_gbs", 6800.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": args.traffic,
-                "kernel": "micro_fp32_kernel<2,3>", "kernel_ms": k_ms,
+                "kernel": "micro_fp32_2d_kernel<3,4> (shared-memory resident)", "kernel_ms": k_ms,
                 "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
                 "hbm_streaming_equivalent": {
                     "GB_per_s": BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9,
@@ -282,6 +282,49 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- micro-batch mode
+def run_micro_only(args, local_rank):
+    """Time hmm_micro_batch alone (the hot path) on a workload of any grid size.
+
+    Prints one JSON line per run: LU/s and the per-launch device time from the
+    library's events on its launch stream.
+    """
+    import torch
+    import workloads as W
+    from paper_2108_09463_gb300 import HMM, build
+    build()
+    torch.cuda.set_device(local_rank)
+    over = {}
+    if args.macro_grid:
+        n = list(args.macro_grid) + [1] * (3 - len(args.macro_grid))
+        over["n_macro"] = tuple(n)
+    if args.box_n:
+        over["box_n"] = args.box_n
+    if args.alpha_micro:
+        over["alpha_micro"] = args.alpha_micro
+    cfg = W.config(args.workload, **over)
+    if args.workload == "c3_2d_uneven" and args.macro_grid:
+        cfg = cfg.replace(eps_field=None, box_n_field=None)
+        eps, nf = W.uneven_eps_and_n(cfg)
+        cfg = cfg.replace(eps_field=eps, box_n_field=nf)
+    prec = 0 if args.precision == "fp64" else 1
+    h = HMM(cfg, precision=prec, kernel_variant=args.variant)
+    M = torch.from_numpy(W.initial_field(cfg)).cuda()
+    H = torch.empty_like(M)
+    for _ in range(args.warmup):
+        h.micro_batch(M, H)
+    ms = []
+    for _ in range(args.steps):
+        h.micro_batch(M, H)
+        ms.append(h.stats()[1])
+    lu = h.stats()[0]
+    h.close()
+    print(json.dumps({"mode": "micro-only", "workload": args.workload, "boxes": cfg.n_points,
+                      "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
+                      "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3),
+                      "ms": ms}), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -325,13 +368,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
+    ap.add_argument("--micro-only", action="store_true",
+                    help="time hmm_micro_batch alone (see --workload, --macro-grid, --precision, --variant)")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--macro-grid", type=int, nargs="+", default=None)
+    ap.add_argument("--box-n", type=int, default=None)
+    ap.add_argument("--alpha-micro", type=float, default=None)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--variant", type=int, default=0, help="FP32 kernel: 0/1 generic, 2 resident 2D")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.micro_only:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.micro_only:
+        run_micro_only(args, local_rank)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)

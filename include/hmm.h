@@ -92,8 +92,9 @@ typedef struct {
   int interp_order;             /* 2k in {2, 4}; <= 0: 4                           */
   int stencil_order;            /* 2 or 4; <= 0: 4                                 */
   int precision;                /* hmm_precision                                   */
-  int kernel_variant;           /* HMM_FP32_BATCHED: 0 or 1 generic arena kernel,
-                                   2 resident 2D kernel (d = 2, N - 2r <= 64)       */
+  int kernel_variant;           /* HMM_FP32_BATCHED kernel: 0 automatic (resident
+                                   2D kernel when d = 2 and N - 2r <= 64, else the
+                                   generic arena kernel), 1 generic, 2 resident    */
   int reserved[4];              /* must be zero                                    */
 } hmm_params;
 

@@ -487,7 +487,7 @@ hmm_status build(HmmHandle* h) {
                       res2d_setup_fits(h->nmax, h->radius, h->interp_k, p.n_terms);
   if (p.kernel_variant == 2 && !res_ok)
     return fail(h, HMM_ERR_INVALID_ARG, "the resident kernel needs FP32, d = 2 and N - 2r <= 64");
-  h->res2d = res_ok && p.kernel_variant == 2;
+  h->res2d = res_ok && p.kernel_variant != 1;
 
   // Launch shape: persistent grid of (CTAs per SM x SMs), capped by the box count.
   int per_sm = 0;

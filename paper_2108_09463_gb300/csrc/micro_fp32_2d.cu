@@ -112,7 +112,7 @@ __device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD
     const float2 C = P[t + R];
     const float2 L1 = *reinterpret_cast<const float2*>(row - 2);
     const float2 R1 = *reinterpret_cast<const float2*>(row + 2);
-    const float* ay = afy_row0 + min(ii0 + t, Ni - 1) * kResLDY;
+    const float* ay = afy_row0 + min(ii0 + t, Ni - 1) * kResLDY + jj0;
     if (R == 3) {
       const float2 L2 = *reinterpret_cast<const float2*>(row - 4);
       const float r2x = row[4];
@@ -429,7 +429,16 @@ int res2d_block(int nmax, int R) {
 template <int R>
 static cudaError_t prepare_r(size_t smem, int* per_sm) {
   auto kern = micro_fp32_2d_kernel<R, kResTR>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, 32 * ((kResMaxInterior + kResTR - 1) / kResTR), smem);
 }

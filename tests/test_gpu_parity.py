@@ -53,9 +53,9 @@ def rel_err(Hg, Hr):
     return np.linalg.norm(d, axis=0).max() / np.linalg.norm(Hr.astype(np.float64), axis=0).max()
 
 
-def gpu_micro(torch, cfg, M0, precision):
+def gpu_micro(torch, cfg, M0, precision, kernel_variant=0):
     from paper_2108_09463_gb300 import HMM
-    h = HMM(cfg, precision=precision)
+    h = HMM(cfg, precision=precision, kernel_variant=kernel_variant)
     M = torch.from_numpy(M0).cuda()
     H = h.micro_batch(M).cpu().numpy()
     info = h.box_info()
@@ -114,6 +114,43 @@ def test_uneven_boxes_parity(torch_cuda, precision):
                      list(np.random.default_rng(0).choice(cfg.n_points, nsample, replace=False))))
     _, Hr = reference(cfg, M0, precision, pts)
     assert rel_err(Hg[:, pts], Hr) < TOL[precision]
+
+
+RESIDENT_2D = ["2d_small", "2d_ragged", "2d_order2", "2d_slow_fast"]
+
+
+@pytest.mark.parametrize("case", RESIDENT_2D)
+def test_resident_2d_kernel_parity(torch_cuda, case):
+    """The shared-memory-resident 2D FP32 kernel (kernel_variant 2) against the FP64 oracle."""
+    name, over = SMALL[case]
+    cfg = W.config(name, **over)
+    if name == "c3_2d_uneven":
+        cfg = cfg.replace(eps_field=None, box_n_field=None)
+    M0 = W.initial_field(cfg)
+    Hg, _ = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    Hr = O.micro_batch(cfg, M0)
+    assert rel_err(Hg, Hr) < TOL[1], (case, rel_err(Hg, Hr))
+
+
+def test_resident_2d_kernel_uneven_boxes(torch_cuda):
+    cfg = _uneven_small()
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    N = info["N"]
+    pts = sorted(set([int(np.argmin(N)), int(np.argmax(N))] +
+                     list(np.random.default_rng(2).choice(cfg.n_points, 10, replace=False))))
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1]
+
+
+def test_resident_2d_kernel_full_size_sampled(torch_cuda):
+    cfg = W.config("c2_2d")
+    M0 = W.initial_field(cfg)
+    Hg, _ = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    assert np.all(np.isfinite(Hg))
+    pts = sorted(set([0, cfg.n_points - 1] + list(np.random.default_rng(3).choice(cfg.n_points, 4, replace=False))))
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1]
 
 
 FULL = [("c2_2d", 0), ("c2_2d", 1), ("c3_2d_uneven", 1)]
