@@ -249,6 +249,7 @@ struct HmmHandle {
   float* d_W32 = nullptr;
   double* d_w64 = nullptr;
   float* d_w32 = nullptr;
+  float* d_om32 = nullptr;
   char* d_arena = nullptr;
   size_t slot_bytes = 0;
   int grid = 0, block = 256;
@@ -292,7 +293,7 @@ hmm_status cuda_fail(HmmHandle* h, cudaError_t e, const char* where) {
 
 void free_all(HmmHandle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_arena, h->d_queue,
+  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue,
                   h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -453,16 +454,26 @@ hmm_status build(HmmHandle* h) {
   HMM_CUDA(h, cudaGetDevice(&h->device));
   HMM_CUDA(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   std::vector<float> W32(W64.begin(), W64.end()), w32(w.begin(), w.end());
+  std::vector<float> om32(w.size() + 1, 0.f);   // Omega_j = sum_{n >= j} w_n (suffix sums in FP64)
+  {
+    double tail = 0.0;
+    for (size_t j = w.size(); j-- > 0;) {
+      tail += w[j];
+      om32[j] = (float)tail;
+    }
+  }
   HMM_CUDA(h, cudaMalloc(&h->d_boxes, sizeof(BoxDesc) * h->P));
   HMM_CUDA(h, cudaMalloc(&h->d_W64, sizeof(double) * W64.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_W32, sizeof(float) * W32.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_w64, sizeof(double) * w.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_w32, sizeof(float) * w32.size()));
+  HMM_CUDA(h, cudaMalloc(&h->d_om32, sizeof(float) * om32.size()));
   HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->P, cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_W64, W64.data(), sizeof(double) * W64.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_W32, W32.data(), sizeof(float) * W32.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_w64, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_w32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_om32, om32.data(), sizeof(float) * om32.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMalloc(&h->d_queue, sizeof(int)));
   HMM_CUDA(h, cudaMalloc(&h->d_err, sizeof(int)));
   HMM_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
@@ -526,6 +537,7 @@ hmm_status build(HmmHandle* h) {
   a.W32 = h->d_W32;
   a.w64 = h->d_w64;
   a.w32 = h->d_w32;
+  a.om32 = h->d_om32;
   a.c0 = p.c0;
   a.n_terms = p.n_terms;
   for (int t = 0; t < p.n_terms; ++t) {

@@ -49,6 +49,7 @@ struct MicroArgs {
   const float* W32;
   const double* w64;     // time weights, msteps + 1
   const float* w32;
+  const float* om32;     // tail sums Omega_j = sum_{n >= j} w_n, j = 0..msteps + 1
   double c0;
   int n_terms;
   TermDev terms[kMaxTerms];

@@ -6,14 +6,26 @@
 // (sum_n w_n) sum_xi W H(m_init) + sum_n w_n sum_xi H(W)(xi) v^n(xi), by the
 // symmetry of the discrete operator on fields that vanish on the ring.
 //
-// Layout: one CTA per box (atomic queue). The box's FP32 state lives in shared
+// Because v^0 = 0, the time sum is taken over the increments of the stored state:
+// sum_n w_n S(v^n) = sum_n Omega_{n+1} S(v^{n+1} - v^n), S(u) = sum_xi H(W) u and
+// Omega_j = sum_{n >= j} w_n. The kernel K0^{p,q} makes the w_n large and of both
+// signs (sum |w_n| is about 24 for p = 3, q = 7), so FP32 rounding in S(v^n) would
+// be amplified; the increments are small, and so are the rounding errors of
+// S(v^{n+1} - v^n).
+//
+// Layout: one CTA per box (atomic queue). The box's FP32 data live in shared
 // memory for all M steps: v^n (vA) and the stage state v^n + dt k1 (vB) on the
-// whole box, m_init and H(m_init) on the interior, and the face coefficients of
-// both axes. Each thread owns a tile of TR rows x 2 adjacent columns; the two
+// whole box; m_init, H(m_init), H(W) and the face coefficients of both axes on
+// the interior. Each thread owns a tile of TR rows x 2 adjacent columns; the two
 // columns are processed together with packed FP32x2 instructions. Per-node
-// registers: k1 (stage 1 -> stage 2), the carried rounding error of v (v_lo, in
-// bf16: it only has to carry a rounding error forward) and H(W) in FP32. The FP64 set-up (m_init, a^eps, H(m_init), H(W)) goes through
-// the CTA's global arena once per box.
+// registers, both in bf16 because each only carries a rounding error forward:
+// the rounding error e_B of the stored stage state v_B = fl(v + dt k1) (stage 2
+// recovers dt k1 = (v_B - v) + e_B exactly, v_B - v being exact by Sterbenz's
+// lemma) and the carried rounding error of v itself (v_lo). The weighted sum of
+// H(W) (v^{n+1} - v^n) is reduced per warp and accumulated (Kahan, with the exact
+// rounding error of each product by Omega) in shared memory. The
+// FP64 set-up (m_init, a^eps, H(m_init), H(W)) goes through the CTA's global
+// arena once per box.
 #include <cuda_bf16.h>
 
 #include "micro_common.cuh"
@@ -22,30 +34,32 @@
 namespace hmm {
 
 constexpr int kResMaxInterior = 64;   // interior columns one warp covers (32 lanes x 2)
-constexpr int kResLDI = 64;           // row stride of interior-only arrays (floats)
-constexpr int kResLDY = 68;           // row stride of the y-face array (>= Ni + 3)
-
-__host__ __device__ inline int res_ld(int nmax) { return (nmax + 4 + 1) & ~1; }
 
 struct ResLayout {
-  int LD;            // row stride of vA/vB
-  size_t vA, vB, mi, hi, afx, afy, red;   // offsets in floats
+  int LD;            // row stride of vA/vB (box rows, column j at offset j + 1)
+  int LDI;           // row stride of interior arrays (>= Ni + 1)
+  int LDY;           // row stride of the y-face array (>= Ni + 2R + 2)
+  size_t vA, vB, mi, hi, hw, afx, afy, kah, red;   // offsets in floats
   size_t total;      // floats
 };
 
 __host__ __device__ inline ResLayout res_layout(int nmax, int R) {
   ResLayout L;
   const int nimax = nmax - 2 * R;
-  const int nfx = nimax + (R == 3 ? 3 : 1);
-  L.LD = res_ld(nmax);
+  const int nfmax = nimax + (R == 3 ? 3 : 1);
+  L.LD = (nmax + 4 + 1) & ~1;
+  L.LDI = (nimax + 1) & ~1;
+  L.LDY = (nfmax + 2) & ~1;
   size_t o = 0;
   L.vA = o; o += (size_t)3 * nmax * L.LD;
   L.vB = o; o += (size_t)3 * nmax * L.LD;
-  L.mi = o; o += (size_t)3 * nimax * kResLDI;
-  L.hi = o; o += (size_t)3 * nimax * kResLDI;
-  L.afx = o; o += (size_t)nfx * kResLDI;
-  L.afy = o; o += (size_t)nimax * kResLDY;
-  o = (o + 1) & ~(size_t)1;          // 8-byte alignment for the doubles
+  L.mi = o; o += (size_t)3 * nimax * L.LDI;
+  L.hi = o; o += (size_t)3 * nimax * L.LDI;
+  L.hw = o; o += (size_t)nimax * L.LDI;
+  L.afx = o; o += (size_t)nfmax * L.LDI;
+  L.afy = o; o += (size_t)nimax * L.LDY;
+  L.kah = o; o += 32 * 6;              // per-warp Kahan sums and compensations
+  o = (o + 1) & ~(size_t)1;            // 8-byte alignment for the doubles
   L.red = o; o += 2 * 96;
   L.total = o;
   return L;
@@ -53,7 +67,7 @@ __host__ __device__ inline ResLayout res_layout(int nmax, int R) {
 
 size_t res2d_smem_bytes(int nmax, int R) { return res_layout(nmax, R).total * sizeof(float); }
 
-// Set-up tables (FP64) overlay the vB region while a box is being set up.
+// The set-up tables (FP64) overlay the vB region while a box is being set up.
 bool res2d_setup_fits(int nmax, int R, int interp_k, int n_terms) {
   const ResLayout L = res_layout(nmax, R);
   return setup_smem_doubles(2, nmax, interp_k, n_terms) * 2 <= (size_t)3 * nmax * L.LD;
@@ -68,67 +82,74 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 shift2(float2 a, float2 b) { return f2(a.y, b.x); }  // (a.y, b.x)
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
 // Stencil of one component at the thread's TR x 2 tile. V: the component plane of
-// vA or vB (row stride LD, column j at offset j + 1). Result H (unscaled) per row.
+// vA or vB (row stride LD, column j at offset j + 1). Result H (without the
+// 1/dx^2 or 1/(24 dx)^2 factor) per row.
 template <int R, int TR>
 __device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD, int N, int i0, int j0,
-                                             const float* __restrict__ afx, int nf, int jj0,
-                                             const float* __restrict__ afy_row0, int ii0, int Ni,
+                                             const float* __restrict__ afx, int LDI, int nf, int jj0,
+                                             const float* __restrict__ afy, int LDY, int ii0, int Ni,
                                              float2* H) {
-  constexpr int NP = TR + 2 * R;          // rows read
-  float2 P[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    const int row = min(i0 - R + k, N - 1);
-    P[k] = *reinterpret_cast<const float2*>(V + row * LD + j0 + 1);
-  }
-  // x direction (rows), faces between rows
+  // x direction (rows): a rolling window over the rows and over the face fluxes.
+  // Each node combines its four fluxes as (F_t - F_{t+3}) + 27 (F_{t+2} - F_{t+1}):
+  // the two differences of neighbouring fluxes cancel with little rounding.
+  auto ld = [&](int k) { return lds2(V + min(i0 - R + k, N - 1) * LD + j0 + 1); };
+  auto axf = [&](int f) { return lds2(afx + min(ii0 + f, nf - 1) * LDI + jj0); };
+  const float2 k27 = f2(27.f, 27.f);
+  float2 Cc[TR];   // centre values of the tile rows (reused by the y direction)
   if (R == 3) {
-    float2 F[TR + 3];
+    float2 p0 = ld(0), p1 = ld(1), p2 = ld(2);
+    float2 Fa = f2(0.f, 0.f), Fb = Fa, Fc = Fa;   // F_{f-3}, F_{f-2}, F_{f-1}
 #pragma unroll
     for (int f = 0; f < TR + 3; ++f) {
-      const float2 g = fma2(f2(27.f, 27.f), sub2(P[f + 2], P[f + 1]), sub2(P[f], P[f + 3]));
-      const float2 ax = *reinterpret_cast<const float2*>(afx + min(ii0 + f, nf - 1) * kResLDI + jj0);
-      F[f] = mul2(ax, g);
+      const float2 p3 = ld(f + 3);
+      if (f < TR) Cc[f] = p3;
+      const float2 F = mul2(axf(f), fma2(k27, sub2(p2, p1), sub2(p0, p3)));
+      if (f >= 3) H[f - 3] = fma2(k27, sub2(Fc, Fb), sub2(Fa, F));
+      Fa = Fb;
+      Fb = Fc;
+      Fc = F;
+      p0 = p1;
+      p1 = p2;
+      p2 = p3;
     }
-#pragma unroll
-    for (int t = 0; t < TR; ++t)
-      H[t] = fma2(f2(27.f, 27.f), sub2(F[t + 2], F[t + 1]), sub2(F[t], F[t + 3]));
   } else {
-    float2 F[TR + 1];
+    float2 p0 = ld(0), Fa = f2(0.f, 0.f);
 #pragma unroll
     for (int f = 0; f < TR + 1; ++f) {
-      const float2 ax = *reinterpret_cast<const float2*>(afx + min(ii0 + f, nf - 1) * kResLDI + jj0);
-      F[f] = mul2(ax, sub2(P[f + 1], P[f]));
+      const float2 p1 = ld(f + 1);
+      if (f < TR) Cc[f] = p1;
+      const float2 F = mul2(axf(f), sub2(p1, p0));
+      if (f >= 1) H[f - 1] = sub2(F, Fa);   // H[t] = F_{t+1} - F_t
+      Fa = F;
+      p0 = p1;
     }
-#pragma unroll
-    for (int t = 0; t < TR; ++t) H[t] = sub2(F[t + 1], F[t]);
   }
   // y direction (columns), faces between columns, row by row
 #pragma unroll
   for (int t = 0; t < TR; ++t) {
     const float* row = V + min(i0 + t, N - 1) * LD + j0 + 1;
-    const float2 C = P[t + R];
-    const float2 L1 = *reinterpret_cast<const float2*>(row - 2);
-    const float2 R1 = *reinterpret_cast<const float2*>(row + 2);
-    const float* ay = afy_row0 + min(ii0 + t, Ni - 1) * kResLDY + jj0;
+    const float2 C = Cc[t];
+    const float2 L1 = lds2(row - 2);
+    const float2 R1 = lds2(row + 2);
+    const float* ay = afy + min(ii0 + t, Ni - 1) * LDY + jj0;
     if (R == 3) {
-      const float2 L2 = *reinterpret_cast<const float2*>(row - 4);
+      const float2 L2 = lds2(row - 4);
       const float r2x = row[4];
-      const float2 a01 = *reinterpret_cast<const float2*>(ay);
-      const float2 a23 = *reinterpret_cast<const float2*>(ay + 2);
+      const float2 a01 = lds2(ay), a23 = lds2(ay + 2);
       const float a4 = ay[4];
       // faces b = j0-2, j0-1 | j0, j0+1 | j0+2
-      const float2 g01 = fma2(f2(27.f, 27.f), sub2(shift2(L1, C), L1), sub2(shift2(L2, L1), C));
-      const float2 g23 = fma2(f2(27.f, 27.f), sub2(shift2(C, R1), C), sub2(shift2(L1, C), R1));
+      const float2 g01 = fma2(k27, sub2(shift2(L1, C), L1), sub2(shift2(L2, L1), C));
+      const float2 g23 = fma2(k27, sub2(shift2(C, R1), C), sub2(shift2(L1, C), R1));
       const float g4 = (C.y - r2x) + 27.f * (R1.y - R1.x);
       const float2 F01 = mul2(a01, g01), F23 = mul2(a23, g23);
       const float F4 = a4 * g4;
-      const float2 hy = fma2(f2(27.f, 27.f), sub2(F23, shift2(F01, F23)), sub2(F01, f2(F23.y, F4)));
+      const float2 hy = fma2(k27, sub2(F23, shift2(F01, F23)), sub2(F01, f2(F23.y, F4)));
       H[t] = add2(H[t], hy);
     } else {
-      const float2 a01 = *reinterpret_cast<const float2*>(ay);
+      const float2 a01 = lds2(ay);
       const float a2 = ay[2];
       const float2 g01 = sub2(C, shift2(L1, C));
       const float g2 = R1.x - C.y;
@@ -153,6 +174,27 @@ __device__ __forceinline__ void ll_rhs2(const float2* m, const float2* H, float2
   f[2] = mul2(fma2(alpha, d2, p2), mone);
 }
 
+// Add w * (warp sum of part[0..2]) to the warp's Kahan accumulators in shared
+// memory (sum kah[c], compensation kah[3 + c]; the total is kah[c] - kah[3 + c]).
+// The product's rounding error e = w x - fl(w x) is exact (one fma) and goes into
+// the compensation. Explicit _rn intrinsics keep the compiler from contracting.
+__device__ __forceinline__ void warp_kahan_add(float* kah, int lane, float w, float* part) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) part[c] = warp_sum(part[c]);
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float p = __fmul_rn(w, part[c]);
+      const float e = __fmaf_rn(w, part[c], -p);
+      const float s = kah[c], cmp = kah[3 + c];
+      const float y = __fsub_rn(p, cmp);
+      const float t = __fadd_rn(s, y);
+      kah[3 + c] = __fsub_rn(__fsub_rn(__fsub_rn(t, s), y), e);
+      kah[c] = t;
+    }
+  }
+}
+
 template <int R, int TR>
 __global__ void __launch_bounds__(32 * ((kResMaxInterior + TR - 1) / TR))
 micro_fp32_2d_kernel(MicroArgs a) {
@@ -161,11 +203,12 @@ micro_fp32_2d_kernel(MicroArgs a) {
   __shared__ int s_box;
   const int nmax = a.nmax;
   const ResLayout Ly = res_layout(nmax, R);
-  const int LD = Ly.LD;
+  const int LD = Ly.LD, LDI = Ly.LDI, LDY = Ly.LDY;
   float* vA = fsm + Ly.vA;
   float* vB = fsm + Ly.vB;
   float* miS = fsm + Ly.mi;
   float* hiS = fsm + Ly.hi;
+  float* hwS = fsm + Ly.hw;
   float* afx = fsm + Ly.afx;
   float* afy = fsm + Ly.afy;
   double* red = reinterpret_cast<double*>(fsm + Ly.red);
@@ -175,6 +218,7 @@ micro_fp32_2d_kernel(MicroArgs a) {
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
+  float* kah = fsm + Ly.kah + 6 * warp;
   const size_t cap = (size_t)nmax * nmax;
   double* mi64 = reinterpret_cast<double*>(a.arena + (size_t)blockIdx.x * a.slot_bytes);
   double* af64 = mi64 + 3 * cap;
@@ -211,9 +255,10 @@ micro_fp32_2d_kernel(MicroArgs a) {
       }
     }
     if (bad) atomicOr(a.err, kErrCoefNonPositive);
+    if (tid < 6 * 32) fsm[Ly.kah + tid] = 0.f;
     __syncthreads();   // the set-up tables (overlaying vB) are no longer needed
 
-    // ---- Shared-memory fields: v = 0, m_init, face coefficients; H(m_init) below.
+    // ---- Shared-memory fields: v = 0, m_init, face coefficients, H(m_init), H(W).
     for (int e = tid; e < 3 * nmax * LD; e += nt) {
       vA[e] = 0.f;
       vB[e] = 0.f;
@@ -223,70 +268,54 @@ micro_fp32_2d_kernel(MicroArgs a) {
     for (int e = tid; e < 3 * Ni * Ni; e += nt) {
       const int c = e / (Ni * Ni), r = e - c * Ni * Ni;
       const int ii = r / Ni, jj = r - ii * Ni;
-      miS[(c * Ni + ii) * kResLDI + jj] = (float)mi64[c * cap + (ii + R) * N + (jj + R)];
+      miS[(c * Ni + ii) * LDI + jj] = (float)mi64[c * cap + (ii + R) * N + (jj + R)];
     }
     for (int e = tid; e < nf * Ni; e += nt) {
       const int f = e / Ni, jj = e - f * Ni;
-      afx[f * kResLDI + jj] = (float)af64[(f + f0) * N + (jj + R)];        // x-face between rows f+f0, f+f0+1
+      afx[f * LDI + jj] = (float)af64[(f + f0) * N + (jj + R)];        // x-face between rows f+f0, f+f0+1
     }
     for (int e = tid; e < Ni * nf; e += nt) {
       const int ii = e / nf, g = e - ii * nf;
-      afy[ii * kResLDY + g] = (float)af64[cap + (ii + R) * N + (g + f0)];   // y-face between columns g+f0, g+f0+1
+      afy[ii * LDY + g] = (float)af64[cap + (ii + R) * N + (g + f0)];   // y-face between columns g+f0, g+f0+1
     }
-
-    // ---- Thread tile: rows i0.., columns j0, j0+1.
-    const int ii0 = warp * TR;                 // first interior row of the tile
-    const int i0 = R + ii0;
-    const int jj0 = 2 * lane;
-    const int j0 = R + jj0;
-    const bool colok = jj0 < Ni;
-    const bool tile_active = colok && ii0 < Ni;
-    const float2 cmask = f2(1.f, (jj0 + 1 < Ni) ? 1.f : 0.f);   // odd Ni: the second column is ring
     const double cs64 = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
     const double* W1d = a.W64 + bd.wofs;
-
-    // H(m_init) (FP64) at the tile's nodes -> hiS; its weighted sum; H(W) -> registers.
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    float2 hw[TR];
+    for (int e = tid; e < Ni * Ni; e += nt) {
+      const int ii = e / Ni, jj = e - ii * Ni;
+      const int idx = (ii + R) * N + (jj + R);
+      double H[3];
+      stencil_H<D, R, double>(mi64, af64, cap, st, idx, cs64, H);
+      const double W = W1d[ii + R] * W1d[jj + R];
+      s0 += W * H[0];
+      s1 += W * H[1];
+      s2 += W * H[2];
 #pragma unroll
-    for (int t = 0; t < TR; ++t) {
-      hw[t] = f2(0.f, 0.f);
-      if (!tile_active || ii0 + t >= Ni) continue;
-      float hwv[2] = {0.f, 0.f};
+      for (int c = 0; c < 3; ++c) hiS[(c * Ni + ii) * LDI + jj] = (float)H[c];
+      // H(W) with the same operator (W vanishes on and near the ring)
+      double hwd = 0.0;
+#pragma unroll 1
+      for (int k = 0; k < D; ++k) {
+        const int s = st.s[k];
+        const double* af = af64 + k * cap;
+        double Wv[7];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (jj0 + q >= Ni) continue;
-        const int idx = (i0 + t) * N + (j0 + q);
-        double H[3];
-        stencil_H<D, R, double>(mi64, af64, cap, st, idx, cs64, H);
-        const double W = W1d[i0 + t] * W1d[j0 + q];
-        s0 += W * H[0];
-        s1 += W * H[1];
-        s2 += W * H[2];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) hiS[(c * Ni + ii0 + t) * kResLDI + jj0 + q] = (float)H[c];
-        // H(W) with the same operator (W vanishes on and near the ring)
-        double hwd = 0.0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const int s = st.s[k];
-          const double* af = af64 + k * cap;
-          auto Wn = [&](int o) {
-            const int id = idx + o * s;
-            const int r_ = id / N, c_ = id - r_ * N;
-            return W1d[r_] * W1d[c_];
-          };
-          if (R == 1) {
-            hwd += af[idx] * (Wn(1) - Wn(0)) - af[idx - s] * (Wn(0) - Wn(-1));
-          } else {
-            const double m_3 = Wn(-3), m_2 = Wn(-2), m_1 = Wn(-1), m0 = Wn(0), m1 = Wn(1), m2 = Wn(2), m3 = Wn(3);
-            hwd += (af[idx - 2 * s] * ((m_3 - m0) + 27.0 * (m_1 - m_2)) - af[idx + s] * ((m0 - m3) + 27.0 * (m2 - m1))) +
-                   27.0 * (af[idx] * ((m_1 - m2) + 27.0 * (m1 - m0)) - af[idx - s] * ((m_2 - m1) + 27.0 * (m0 - m_1)));
-          }
+        for (int o = -R; o <= R; ++o) {
+          const int id = idx + o * s;
+          const int r_ = id / N, c_ = id - r_ * N;
+          Wv[o + R] = W1d[r_] * W1d[c_];
         }
-        hwv[q] = (float)(hwd * cs64);
+        if (R == 1) {
+          hwd += af[idx] * (Wv[2] - Wv[1]) - af[idx - s] * (Wv[1] - Wv[0]);
+        } else {
+          const double g_2 = (Wv[0] - Wv[3]) + 27.0 * (Wv[2] - Wv[1]);
+          const double g_1 = (Wv[1] - Wv[4]) + 27.0 * (Wv[3] - Wv[2]);
+          const double g0 = (Wv[2] - Wv[5]) + 27.0 * (Wv[4] - Wv[3]);
+          const double g1 = (Wv[3] - Wv[6]) + 27.0 * (Wv[5] - Wv[4]);
+          hwd += (af[idx - 2 * s] * g_2 - af[idx + s] * g1) + 27.0 * (af[idx] * g0 - af[idx - s] * g_1);
+        }
       }
-      hw[t] = f2(hwv[0], hwv[1]);
+      hwS[ii * LDI + jj] = (float)(hwd * cs64);
     }
     {
       double wsum = 0.0;
@@ -297,94 +326,85 @@ micro_fp32_2d_kernel(MicroArgs a) {
     }
     __syncthreads();
 
-    // ---- Time loop.
+    // ---- Thread tile: rows i0 .. i0+TR-1, columns j0, j0+1.
+    const int ii0 = warp * TR;
+    const int i0 = R + ii0;
+    const int jj0 = 2 * lane;
+    const int j0 = R + jj0;
+    const bool tile_active = jj0 < Ni && ii0 < Ni;
+    const float2 cmask = f2(1.f, (jj0 + 1 < Ni) ? 1.f : 0.f);   // odd Ni: the second column is ring
     const float csf = (float)cs64;
     const float2 cs2 = f2(csf, csf);
     const float dtf = (float)bd.dt;
     const float2 dt2 = f2(dtf, dtf), hdt2 = f2(0.5f * dtf, 0.5f * dtf);
-    float2 k1[3][TR];
-    __nv_bfloat162 vlo[3][TR];
+    __nv_bfloat162 eB[3][TR], vlo[3][TR];
 #pragma unroll
     for (int t = 0; t < TR; ++t)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) vlo[c][t] = __float2bfloat162_rn(0.f);
-    float ks[3] = {0.f, 0.f, 0.f}, kc[3] = {0.f, 0.f, 0.f};
-
-    for (int n = 0; n <= a.msteps; ++n) {
-      const float wn = a.w32[n];
-      if (tile_active) {
-        // The weighted sum of H(W) v^n (eq. upscaling through the operator's symmetry).
-        float part[3] = {0.f, 0.f, 0.f};
-        if (wn != 0.f) {
-#pragma unroll
-          for (int t = 0; t < TR; ++t) {
-            if (ii0 + t >= Ni) continue;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float2 v = *reinterpret_cast<const float2*>(vA + (c * nmax + i0 + t) * LD + j0 + 1);
-              const float2 p = mul2(hw[t], v);
-              part[c] += p.x + p.y;
-            }
-          }
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float y = wn * part[c] - kc[c];
-            const float tt = ks[c] + y;
-            kc[c] = (tt - ks[c]) - y;
-            ks[c] = tt;
-          }
-        }
+      for (int c = 0; c < 3; ++c) {
+        vlo[c][t] = __float2bfloat162_rn(0.f);
+        eB[c][t] = __float2bfloat162_rn(0.f);
       }
-      if (n == a.msteps) break;
+    const float2 half2 = f2(0.5f, 0.5f);
+
+    for (int n = 0; n < a.msteps; ++n) {
+      const float om = a.om32[n + 1];
       if (tile_active) {
         // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
         float2 Hs[3][TR];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          tile_stencil<R, TR>(vA + c * nmax * LD, LD, N, i0, j0, afx, nf, jj0, afy, ii0, Ni, Hs[c]);
+          tile_stencil<R, TR>(vA + c * nmax * LD, LD, N, i0, j0, afx, LDI, nf, jj0, afy, LDY, ii0, Ni, Hs[c]);
 #pragma unroll
         for (int t = 0; t < TR; ++t) {
           if (ii0 + t >= Ni) continue;
+          const int ro = (ii0 + t) * LDI + jj0;
           float2 v[3], m[3], H[3], f[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            v[c] = *reinterpret_cast<const float2*>(vA + (c * nmax + i0 + t) * LD + j0 + 1);
-            m[c] = add2(*reinterpret_cast<const float2*>(miS + (c * Ni + ii0 + t) * kResLDI + jj0), v[c]);
-            H[c] = fma2(Hs[c][t], cs2, *reinterpret_cast<const float2*>(hiS + (c * Ni + ii0 + t) * kResLDI + jj0));
+            v[c] = lds2(vA + (c * nmax + i0 + t) * LD + j0 + 1);
+            m[c] = add2(lds2(miS + c * Ni * LDI + ro), v[c]);
+            H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * Ni * LDI + ro));
           }
           ll_rhs2(m, H, alpha2, f);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            k1[c][t] = f[c];
-            *reinterpret_cast<float2*>(vB + (c * nmax + i0 + t) * LD + j0 + 1) = mul2(fma2(dt2, f[c], v[c]), cmask);
+            const float2 delta = mul2(dt2, f[c]);
+            const float2 vb = add2(v[c], delta);
+            eB[c][t] = __float22bfloat162_rn(sub2(delta, sub2(vb, v[c])));
+            *reinterpret_cast<float2*>(vB + (c * nmax + i0 + t) * LD + j0 + 1) = mul2(vb, cmask);
           }
         }
       }
-      if (n == a.msteps) break;
       __syncthreads();
+      float part[3] = {0.f, 0.f, 0.f};
       if (tile_active) {
         // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
         float2 Hs[3][TR];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          tile_stencil<R, TR>(vB + c * nmax * LD, LD, N, i0, j0, afx, nf, jj0, afy, ii0, Ni, Hs[c]);
+          tile_stencil<R, TR>(vB + c * nmax * LD, LD, N, i0, j0, afx, LDI, nf, jj0, afy, LDY, ii0, Ni, Hs[c]);
 #pragma unroll
         for (int t = 0; t < TR; ++t) {
           if (ii0 + t >= Ni) continue;
-          float2 mi[3], m[3], H[3], k2[3], vh[3], d[3], vt[3];
+          const int ro = (ii0 + t) * LDI + jj0;
+          float2 mi[3], m[3], H[3], k2[3], vh[3], d[3], vt[3], vbo[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            mi[c] = *reinterpret_cast<const float2*>(miS + (c * Ni + ii0 + t) * kResLDI + jj0);
-            m[c] = add2(mi[c], *reinterpret_cast<const float2*>(vB + (c * nmax + i0 + t) * LD + j0 + 1));
-            H[c] = fma2(Hs[c][t], cs2, *reinterpret_cast<const float2*>(hiS + (c * Ni + ii0 + t) * kResLDI + jj0));
+            mi[c] = lds2(miS + c * Ni * LDI + ro);
+            vbo[c] = lds2(vB + (c * nmax + i0 + t) * LD + j0 + 1);
+            m[c] = add2(mi[c], vbo[c]);
+            H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * Ni * LDI + ro));
           }
           ll_rhs2(m, H, alpha2, k2);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            vh[c] = *reinterpret_cast<const float2*>(vA + (c * nmax + i0 + t) * LD + j0 + 1);
-            d[c] = mul2(hdt2, add2(k1[c][t], k2[c]));
+            vh[c] = lds2(vA + (c * nmax + i0 + t) * LD + j0 + 1);
+            // dt/2 (k1 + k2) with dt k1 = (v_B - v) + e_B
+            d[c] = fma2(hdt2, k2[c], mul2(half2, add2(sub2(vbo[c], vh[c]), __bfloat1622float2(eB[c][t]))));
             vt[c] = add2(vh[c], d[c]);
           }
+          const float2 hw = lds2(hwS + ro);
           // s = 2 m_init.vt + |vt|^2; c = -s / (sqrt(1+s)(1+sqrt(1+s)))
           float2 sdot = mul2(mi[0], vt[0]);
           sdot = fma2(mi[1], vt[1], sdot);
@@ -400,15 +420,24 @@ micro_fp32_2d_kernel(MicroArgs a) {
             const float2 inc = add2(fma2(cf, add2(mi[c], vt[c]), d[c]), __bfloat1622float2(vlo[c][t]));
             const float2 nh = add2(vh[c], inc);
             vlo[c][t] = __float22bfloat162_rn(sub2(inc, sub2(nh, vh[c])));
-            *reinterpret_cast<float2*>(vA + (c * nmax + i0 + t) * LD + j0 + 1) = mul2(nh, cmask);
+            const float2 nv = mul2(nh, cmask);
+            *reinterpret_cast<float2*>(vA + (c * nmax + i0 + t) * LD + j0 + 1) = nv;
+            // H(W) times the exact change of the stored state (zero in a ring column)
+            const float2 pr = mul2(hw, sub2(nv, vh[c]));
+            part[c] += pr.x + pr.y;
           }
         }
       }
+      if (om != 0.f) warp_kahan_add(kah, lane, om, part);
       __syncthreads();
     }
-    double acc0 = s0 + ((double)ks[0] - (double)kc[0]);
-    double acc1 = s1 + ((double)ks[1] - (double)kc[1]);
-    double acc2 = s2 + ((double)ks[2] - (double)kc[2]);
+
+    double acc0 = s0, acc1 = s1, acc2 = s2;
+    if (lane == 0) {
+      acc0 += (double)kah[0] - (double)kah[3];
+      acc1 += (double)kah[1] - (double)kah[4];
+      acc2 += (double)kah[2] - (double)kah[5];
+    }
     block_sum3(acc0, acc1, acc2, red);
     if (tid == 0) {
       a.Havg[bd.p] = acc0;

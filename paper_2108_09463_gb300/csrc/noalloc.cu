@@ -256,6 +256,7 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
   a.W32 = reinterpret_cast<const float*>(base + o_W32);
   a.w64 = reinterpret_cast<const double*>(base + o_w64);
   a.w32 = reinterpret_cast<const float*>(base + o_w32);
+  a.om32 = nullptr;   // used by the shared-memory-resident 2D kernel only
   a.c0 = p.c0;
   a.n_terms = p.n_terms;
   for (int t = 0; t < p.n_terms; ++t) {
