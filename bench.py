@@ -318,11 +318,24 @@ def run_micro_only(args, local_rank):
         h.micro_batch(M, H)
         ms.append(h.stats()[1])
     lu = h.stats()[0]
+    rec = {"mode": "micro-only", "workload": args.workload, "boxes": cfg.n_points,
+           "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
+           "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3), "ms": ms}
+    if args.macro_steps > 0:
+        # steady-state macro steps (MPEA, one micro batch each, graph replay) after
+        # the RK4P start-up steps j = 0, 1 and one warm-up step
+        h.macro_step(M, 3)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        h.macro_step(M, args.macro_steps)
+        t1.record()
+        torch.cuda.synchronize()
+        sec = t0.elapsed_time(t1) / 1e3
+        rec.update(macro_steps=args.macro_steps, macro_steps_per_s=args.macro_steps / sec)
     h.close()
-    print(json.dumps({"mode": "micro-only", "workload": args.workload, "boxes": cfg.n_points,
-                      "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
-                      "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3),
-                      "ms": ms}), flush=True)
+    print(json.dumps(rec), flush=True)
 
 
 # ---------------------------------------------------------------- reference arm
@@ -376,6 +389,8 @@ def main():
     ap.add_argument("--alpha-micro", type=float, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--variant", type=int, default=0, help="FP32 kernel: 0/1 generic, 2 resident 2D")
+    ap.add_argument("--macro-steps", type=int, default=0,
+                    help="with --micro-only: also time this many steady-state macro steps")
     args = ap.parse_args()
     if args.warmup < 3 and not args.micro_only:
         ap.error("--warmup must be >= 3")

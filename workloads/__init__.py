@@ -118,7 +118,9 @@ def fourier_field(cfg: HMMConfig, seed: int, kmax: int = 4, sigma: float = 0.5,
 
     m~_c(x) = o_c + sum_{0<|k|<=kmax} sigma/(1+|k|^2) (A cos 2pi k.x + B sin 2pi k.x)
     with A, B ~ N(0,1) drawn from numpy PCG64(seed); redrawn while
-    min |m~| < min_norm, then normalised pointwise (assumption A3).
+    min |m~| < min_norm, with sigma multiplied by 0.7 after every 16 rejected
+    draws (2D fields pass within the first 16; 3D fields at sigma = 0.5 dip below
+    min_norm somewhere on the grid), then normalised pointwise (assumption A3).
     """
     d = cfg.dim
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -129,7 +131,9 @@ def fourier_field(cfg: HMMConfig, seed: int, kmax: int = 4, sigma: float = 0.5,
     amp = sigma / (1.0 + (ks ** 2).sum(1))
     X = _grid(cfg)
     shape = X[0].shape
-    for _attempt in range(64):
+    for attempt in range(128):
+        if attempt and attempt % 16 == 0:
+            amp = 0.7 * amp        # a field this rough keeps dipping below min_norm: make it smoother
         A = rng.standard_normal((3, len(ks)))
         B = rng.standard_normal((3, len(ks)))
         mt = np.empty((3,) + shape)
@@ -144,6 +148,7 @@ def fourier_field(cfg: HMMConfig, seed: int, kmax: int = 4, sigma: float = 0.5,
             mt[c] = acc
         nrm = np.sqrt((mt ** 2).sum(0))
         if nrm.min() >= min_norm:
+            fourier_field.last_attempt = attempt
             return mt / nrm
     raise RuntimeError("fourier_field: could not draw a field with min |m| >= min_norm")
 
