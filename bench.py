@@ -47,25 +47,26 @@ def _peaks():
 
 # ---------------------------------------------------------------- CPU oracle leg
 def _oracle_chunk(args):
-    name, points = args
+    name, over, points = args
     import workloads as W
     from oracle import hmm_oracle as O
-    cfg = W.config(name)
+    cfg = W.config(name, **over)
     M0 = W.initial_field(cfg)
     t = time.perf_counter()
     O.micro_batch(cfg, M0, points=points)
     return time.perf_counter() - t
 
 
-def oracle_sample(name: str, boxes_per_worker: int, workers: int, pool=None):
+def oracle_sample(name: str, boxes_per_worker: int, workers: int, pool=None, over=None):
     """Time the oracle on a bounded sample of boxes of the workload; returns (LU/s, info)."""
     import workloads as W
     from oracle import hmm_oracle as O
-    cfg = W.config(name)
+    over = dict(over or {})
+    cfg = W.config(name, **over)
     n = workers * boxes_per_worker
     stride = max(1, cfg.n_points // n)
     pts = [i * stride for i in range(n)]
-    chunks = [(name, pts[w * boxes_per_worker:(w + 1) * boxes_per_worker]) for w in range(workers)]
+    chunks = [(name, over, pts[w * boxes_per_worker:(w + 1) * boxes_per_worker]) for w in range(workers)]
     t0 = time.perf_counter()
     if pool is None:
         for c in chunks:
@@ -321,6 +322,14 @@ def run_micro_only(args, local_rank):
     rec = {"mode": "micro-only", "workload": args.workload, "boxes": cfg.n_points,
            "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
            "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3), "ms": ms}
+    if args.cpu_baseline_micro:
+        # the oracle on a spread sample of the same boxes, spawned processes on the host cores
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(args.cpu_workers) as pool:
+            oracle_sample(args.workload, 1, args.cpu_workers, pool, over)   # warm the workers
+            v, info = oracle_sample(args.workload, args.cpu_boxes_per_worker, args.cpu_workers, pool, over)
+        rec["cpu_baseline"] = {"value": v, "unit": "LU/s", "cores": args.cpu_workers, "kind": "oracle",
+                               "sample": f"{info['boxes']} of the {cfg.n_points} boxes, {info['wall_s']:.1f} s wall"}
     if args.macro_steps > 0:
         # steady-state macro steps (MPEA, one micro batch each, graph replay) after
         # the RK4P start-up steps j = 0, 1 and one warm-up step
@@ -389,6 +398,8 @@ def main():
     ap.add_argument("--alpha-micro", type=float, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--variant", type=int, default=0, help="FP32 kernel: 0/1 generic, 2 resident 2D")
+    ap.add_argument("--cpu-baseline-micro", action="store_true",
+                    help="with --micro-only: also time the oracle on a sample of the boxes")
     ap.add_argument("--macro-steps", type=int, default=0,
                     help="with --micro-only: also time this many steady-state macro steps")
     args = ap.parse_args()
