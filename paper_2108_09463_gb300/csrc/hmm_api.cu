@@ -219,6 +219,7 @@ void set_null_handle_error(const char* msg) {
 namespace {
 
 constexpr double kMacroDtConstant = 0.06;
+constexpr int kQueues = 32;           // queue counters (one per resident-kernel launch group)
 
 }  // namespace
 
@@ -255,6 +256,8 @@ struct HmmHandle {
   int grid = 0, block = 256;
   size_t smem = 0;
   bool res2d = false;        // resident 2D FP32 kernel
+  Res2dPlan plan;            // its work items and launches
+  int2* d_items = nullptr;
   int* d_queue = nullptr;
   int* d_err = nullptr;
   int* h_err = nullptr;      // pinned
@@ -293,7 +296,7 @@ hmm_status cuda_fail(HmmHandle* h, cudaError_t e, const char* where) {
 
 void free_all(HmmHandle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue,
+  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue, h->d_items,
                   h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -474,7 +477,7 @@ hmm_status build(HmmHandle* h) {
   HMM_CUDA(h, cudaMemcpy(h->d_w64, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_w32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_om32, om32.data(), sizeof(float) * om32.size(), cudaMemcpyHostToDevice));
-  HMM_CUDA(h, cudaMalloc(&h->d_queue, sizeof(int)));
+  HMM_CUDA(h, cudaMalloc(&h->d_queue, sizeof(int) * kQueues));
   HMM_CUDA(h, cudaMalloc(&h->d_err, sizeof(int)));
   HMM_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
   HMM_CUDA(h, cudaMallocHost(&h->h_err, sizeof(int)));
@@ -493,20 +496,23 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim == 2 && h->nmax - 2 * h->radius <= 64 &&
-                      res2d_smem_bytes(h->nmax, h->radius) + 64 <= (size_t)optin &&
-                      res2d_setup_fits(h->nmax, h->radius, h->interp_k, p.n_terms);
-  if (p.kernel_variant == 2 && !res_ok)
-    return fail(h, HMM_ERR_INVALID_ARG, "the resident kernel needs FP32, d = 2 and N - 2r <= 64");
+  std::string why = "the resident kernel needs the FP32 form and d = 2";
+  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim == 2 &&
+                      res2d_make_plan(h->boxes.data(), h->P, h->radius, h->interp_k, p.n_terms,
+                                      (size_t)optin - 256, &h->plan, &why) &&
+                      (int)h->plan.groups.size() <= kQueues;
+  if (p.kernel_variant == 2 && !res_ok) return fail(h, HMM_ERR_INVALID_ARG, why.c_str());
   h->res2d = res_ok && p.kernel_variant != 1;
 
   // Launch shape: persistent grid of (CTAs per SM x SMs), capped by the box count.
   int per_sm = 0;
   if (h->res2d) {
-    h->block = res2d_block(h->nmax, h->radius);
-    h->smem = res2d_smem_bytes(h->nmax, h->radius);
-    HMM_CUDA(h, prepare_micro_fp32_2d(h->radius, h->smem, &per_sm));
+    HMM_CUDA(h, res2d_prepare(h->radius, &h->plan, h->num_sms));
     h->slot_bytes = res2d_slot_bytes(h->nmax);
+    HMM_CUDA(h, cudaMalloc(&h->d_items, sizeof(int2) * h->plan.items.size()));
+    HMM_CUDA(h, cudaMemcpy(h->d_items, h->plan.items.data(), sizeof(int2) * h->plan.items.size(),
+                           cudaMemcpyHostToDevice));
+    per_sm = 1;
   } else {
     h->block = 256;
     h->smem = micro_smem_bytes(h->dim, h->nmax, h->interp_k, p.n_terms);
@@ -517,7 +523,7 @@ hmm_status build(HmmHandle* h) {
                                                   : micro_slot_bytes_fp32(h->dim, h->nmax);
   }
   if (per_sm < 1) return fail(h, HMM_ERR_INVALID_ARG, "micro kernel does not fit on an SM for this box size");
-  h->grid = std::min(h->P, per_sm * h->num_sms);
+  h->grid = h->res2d ? res2d_max_grid(h->plan) : std::min(h->P, per_sm * h->num_sms);
   HMM_CUDA(h, cudaMalloc(&h->d_arena, h->slot_bytes * (size_t)h->grid));
 
   MicroArgs& a = h->args;
@@ -559,11 +565,11 @@ hmm_status build(HmmHandle* h) {
 
 // Enqueue one micro batch (no synchronisation).
 hmm_status enqueue_micro(HmmHandle* h, const double* M, double* Havg) {
-  HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+  HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int) * kQueues, h->stream));
   MicroArgs a = h->args;
   a.M = M;
   a.Havg = Havg;
-  cudaError_t e = h->res2d ? launch_micro_fp32_2d(a, h->radius, h->grid, h->block, h->smem, h->stream)
+  cudaError_t e = h->res2d ? res2d_launch(a, h->radius, h->plan, h->d_items, h->d_queue, h->stream)
                  : h->p.precision == HMM_FP64_PLAIN
                       ? launch_micro_fp64(a, h->dim, h->radius, h->grid, h->block, h->smem, h->stream)
                       : launch_micro_fp32(a, h->dim, h->radius, h->grid, h->block, h->smem, h->stream);

@@ -4,6 +4,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 namespace hmm {
 
 constexpr int kMaxTerms = 8;
@@ -72,14 +75,30 @@ size_t micro_smem_bytes(int dim, int nmax, int interp_k, int n_terms);
 cudaError_t prepare_micro_fp64(int dim, int radius, int block, size_t smem, int* ctas_per_sm);
 cudaError_t prepare_micro_fp32(int dim, int radius, int block, size_t smem, int* ctas_per_sm);
 
-// Resident 2D FP32 kernel (micro_fp32_2d.cu).
-size_t res2d_smem_bytes(int nmax, int R);
-bool res2d_setup_fits(int nmax, int R, int interp_k, int n_terms);
+// Resident 2D FP32 kernel (micro_fp32_2d.cu). The sorted box table is cut into
+// work items (first box, box count): packs of small boxes sharing one CTA, or single
+// boxes shared by a cluster of cs CTAs; items of one cluster size form a group, run
+// as one persistent launch with its own queue counter.
+struct Res2dGroup {
+  int cs;           // CTAs per cluster (1: packs)
+  int variant;      // compiled instance of the kernel
+  int first_item;
+  int n_items;
+  int grid;         // CTAs launched (a multiple of cs), set by res2d_prepare
+};
+struct Res2dPlan {
+  std::vector<int2> items;
+  std::vector<Res2dGroup> groups;
+  size_t smem = 0;  // dynamic shared memory per CTA
+};
+// False (with the reason) when some box fits no cluster of the portable size.
+bool res2d_make_plan(const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
+                     Res2dPlan* plan, std::string* why);
+cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms);
+int res2d_max_grid(const Res2dPlan& plan);
 size_t res2d_slot_bytes(int nmax);
-int res2d_block(int nmax, int R);
-cudaError_t prepare_micro_fp32_2d(int radius, size_t smem, int* ctas_per_sm);
-cudaError_t launch_micro_fp32_2d(const MicroArgs& a, int radius, int grid, int block, size_t smem,
-                                 cudaStream_t st);
+cudaError_t res2d_launch(const MicroArgs& a, int radius, const Res2dPlan& plan, const int2* d_items,
+                         int* d_queues, cudaStream_t st);
 
 // Macro-side kernels (FP64, pointwise over P points).
 cudaError_t launch_h_term(const double* M, const double* H, double alpha, double* h, int P,

@@ -1,485 +1,183 @@
-// Batched FP32 micro kernel for 2D boxes held entirely on chip.
-//
-// Same mathematics and perturbation form as micro_fp32.cu (see there): v = m -
-// m_init stepped by HeunP (Section 3.1) under H(m) = H(m_init) + H(v), the
-// Dirichlet ring v = 0 (Section 4.2), the average of eq. upscaling evaluated as
-// (sum_n w_n) sum_xi W H(m_init) + sum_n w_n sum_xi H(W)(xi) v^n(xi), by the
-// symmetry of the discrete operator on fields that vanish on the ring.
-//
-// Because v^0 = 0, the time sum is taken over the increments of the stored state:
-// sum_n w_n S(v^n) = sum_n Omega_{n+1} S(v^{n+1} - v^n), S(u) = sum_xi H(W) u and
-// Omega_j = sum_{n >= j} w_n. The kernel K0^{p,q} makes the w_n large and of both
-// signs (sum |w_n| is about 24 for p = 3, q = 7), so FP32 rounding in S(v^n) would
-// be amplified; the increments are small, and so are the rounding errors of
-// S(v^{n+1} - v^n).
-//
-// Layout: one CTA per box (atomic queue). The box's FP32 data live in shared
-// memory for all M steps: v^n (vA) and the stage state v^n + dt k1 (vB) on the
-// whole box; m_init, H(m_init), H(W) and the face coefficients of both axes on
-// the interior. Each thread owns a tile of TR rows x 2 adjacent columns; the two
-// columns are processed together with packed FP32x2 instructions. Per-node
-// registers, both in bf16 because each only carries a rounding error forward:
-// the rounding error e_B of the stored stage state v_B = fl(v + dt k1) (stage 2
-// recovers dt k1 = (v_B - v) + e_B exactly, v_B - v being exact by Sterbenz's
-// lemma) and the carried rounding error of v itself (v_lo). The weighted sum of
-// H(W) (v^{n+1} - v^n) is reduced per warp and accumulated (Kahan, with the exact
-// rounding error of each product by Omega) in shared memory. The
-// FP64 set-up (m_init, a^eps, H(m_init), H(W)) goes through the CTA's global
-// arena once per box.
-#include <cuda_bf16.h>
+// Host side of the resident 2D FP32 kernel (micro_fp32_2d.cuh): which compiled
+// instance and cluster size serve each box, the work items (packs of small boxes,
+// single boxes for clusters), the launch shapes and the launches.
+#include <algorithm>
+#include <string>
+#include <vector>
 
-#include "micro_common.cuh"
-#include "stencil.cuh"
+#include "micro_fp32_2d.cuh"
 
 namespace hmm {
 
-constexpr int kResMaxInterior = 64;   // interior columns one warp covers (32 lanes x 2)
-
-struct ResLayout {
-  int LD;            // row stride of vA/vB (box rows, column j at offset j + 1)
-  int LDI;           // row stride of interior arrays (>= Ni + 1)
-  int LDY;           // row stride of the y-face array (>= Ni + 2R + 2)
-  size_t vA, vB, mi, hi, hw, afx, afy, kah, red;   // offsets in floats
-  size_t total;      // floats
-};
-
-__host__ __device__ inline ResLayout res_layout(int nmax, int R) {
-  ResLayout L;
-  const int nimax = nmax - 2 * R;
-  const int nfmax = nimax + (R == 3 ? 3 : 1);
-  L.LD = (nmax + 4 + 1) & ~1;
-  L.LDI = (nimax + 1) & ~1;
-  L.LDY = (nfmax + 2) & ~1;
-  size_t o = 0;
-  L.vA = o; o += (size_t)3 * nmax * L.LD;
-  L.vB = o; o += (size_t)3 * nmax * L.LD;
-  L.mi = o; o += (size_t)3 * nimax * L.LDI;
-  L.hi = o; o += (size_t)3 * nimax * L.LDI;
-  L.hw = o; o += (size_t)nimax * L.LDI;
-  L.afx = o; o += (size_t)nfmax * L.LDI;
-  L.afy = o; o += (size_t)nimax * L.LDY;
-  L.kah = o; o += 32 * 6;              // per-warp Kahan sums and compensations
-  o = (o + 1) & ~(size_t)1;            // 8-byte alignment for the doubles
-  L.red = o; o += 2 * 96;
-  L.total = o;
-  return L;
-}
-
-size_t res2d_smem_bytes(int nmax, int R) { return res_layout(nmax, R).total * sizeof(float); }
-
-// The set-up tables (FP64) overlay the vB region while a box is being set up.
-bool res2d_setup_fits(int nmax, int R, int interp_k, int n_terms) {
-  const ResLayout L = res_layout(nmax, R);
-  return setup_smem_doubles(2, nmax, interp_k, n_terms) * 2 <= (size_t)3 * nmax * L.LD;
-}
-
-__host__ __device__ inline size_t res2d_arena_doubles(int nmax) { return (size_t)5 * nmax * nmax; }
 size_t res2d_slot_bytes(int nmax) { return (res2d_arena_doubles(nmax) * 8 + 255) & ~(size_t)255; }
 
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 shift2(float2 a, float2 b) { return f2(a.y, b.x); }  // (a.y, b.x)
-__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+namespace {
 
-// Stencil of one component at the thread's TR x 2 tile. V: the component plane of
-// vA or vB (row stride LD, column j at offset j + 1). Result H (without the
-// 1/dx^2 or 1/(24 dx)^2 factor) per row.
-template <int R, int TR>
-__device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD, int N, int i0, int j0,
-                                             const float* __restrict__ afx, int LDI, int nf, int jj0,
-                                             const float* __restrict__ afy, int LDY, int ii0, int Ni,
-                                             float2* H) {
-  // x direction (rows): a rolling window over the rows and over the face fluxes.
-  // Each node combines its four fluxes as (F_t - F_{t+3}) + 27 (F_{t+2} - F_{t+1}):
-  // the two differences of neighbouring fluxes cancel with little rounding.
-  auto ld = [&](int k) { return lds2(V + min(i0 - R + k, N - 1) * LD + j0 + 1); };
-  auto axf = [&](int f) { return lds2(afx + min(ii0 + f, nf - 1) * LDI + jj0); };
-  const float2 k27 = f2(27.f, 27.f);
-  float2 Cc[TR];   // centre values of the tile rows (reused by the y direction)
-  if (R == 3) {
-    float2 p0 = ld(0), p1 = ld(1), p2 = ld(2);
-    float2 Fa = f2(0.f, 0.f), Fb = Fa, Fc = Fa;   // F_{f-3}, F_{f-2}, F_{f-1}
-#pragma unroll
-    for (int f = 0; f < TR + 3; ++f) {
-      const float2 p3 = ld(f + 3);
-      if (f < TR) Cc[f] = p3;
-      const float2 F = mul2(axf(f), fma2(k27, sub2(p2, p1), sub2(p0, p3)));
-      if (f >= 3) H[f - 3] = fma2(k27, sub2(Fc, Fb), sub2(Fa, F));
-      Fa = Fb;
-      Fb = Fc;
-      Fc = F;
-      p0 = p1;
-      p1 = p2;
-      p2 = p3;
+const std::vector<ResVariant>& variants() {
+  static const std::vector<ResVariant> all = [] {
+    std::vector<ResVariant> v;
+    int (*getters[])(const ResVariant**) = {res2d_variants_pack, res2d_variants_cluster_a,
+                                            res2d_variants_cluster_b, res2d_variants_any};
+    for (auto g : getters) {
+      const ResVariant* t = nullptr;
+      const int n = g(&t);
+      v.insert(v.end(), t, t + n);
     }
-  } else {
-    float2 p0 = ld(0), Fa = f2(0.f, 0.f);
-#pragma unroll
-    for (int f = 0; f < TR + 1; ++f) {
-      const float2 p1 = ld(f + 1);
-      if (f < TR) Cc[f] = p1;
-      const float2 F = mul2(axf(f), sub2(p1, p0));
-      if (f >= 1) H[f - 1] = sub2(F, Fa);   // H[t] = F_{t+1} - F_t
-      Fa = F;
-      p0 = p1;
+    return v;
+  }();
+  return all;
+}
+
+ResDims geom(const ResVariant& v, int N, int Sa) {
+  return v.NC > 0 ? res_dims(v.NC, v.R, v.SAC) : res_dims(N, v.R, Sa);
+}
+
+// A slab of Sa rows of a box of N nodes under geometry d fits one CTA: shared
+// memory (with the header), threads, and the set-up tables inside the vB region.
+bool slab_fits(const ResDims& d, int N, int R, int Sa, int interp_k, int n_terms, size_t budget_floats) {
+  const int Ni = N - 2 * R;
+  return (size_t)res_offsets(d).total + kResHeaderFloats <= budget_floats &&
+         (res_tiles(Sa, Ni) + 31) / 32 * 32 <= kResThreads && res_setup_fits(d, N, interp_k, n_terms);
+}
+
+bool cluster_ok(int cs, int Sa, int Ni, int R) {
+  return cs == 1 || ((cs - 1) * Sa < Ni && Sa >= R);   // every rank has rows; halos from one neighbour
+}
+
+// The instance and cluster size for a box: the first canvas (table order: growing
+// canvases) that holds it, else the box-stride instance with the smallest cluster.
+bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out) {
+  const auto& V = variants();
+  const int Ni = N - 2 * R;
+  for (int i = 0; i < (int)V.size(); ++i) {
+    const ResVariant& v = V[i];
+    if (v.R != R || v.NC == 0 || v.NC < N) continue;
+    const int Sa = (Ni + v.cs - 1) / v.cs;
+    if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
+    if (!slab_fits(geom(v, N, Sa), N, R, Sa, interp_k, n_terms, budget)) continue;
+    *vi = i;
+    *cs_out = v.cs;
+    return true;
+  }
+  for (int i = 0; i < (int)V.size(); ++i) {
+    const ResVariant& v = V[i];
+    if (v.R != R || v.NC != 0) continue;
+    for (int cs = 1; cs <= kResMaxCluster; ++cs) {
+      const int Sa = (Ni + cs - 1) / cs;
+      if (!cluster_ok(cs, Sa, Ni, R)) continue;
+      if (!slab_fits(geom(v, N, Sa), N, R, Sa, interp_k, n_terms, budget)) continue;
+      *vi = i;
+      *cs_out = cs;
+      return true;
     }
   }
-  // y direction (columns), faces between columns, row by row
-#pragma unroll
-  for (int t = 0; t < TR; ++t) {
-    const float* row = V + min(i0 + t, N - 1) * LD + j0 + 1;
-    const float2 C = Cc[t];
-    const float2 L1 = lds2(row - 2);
-    const float2 R1 = lds2(row + 2);
-    const float* ay = afy + min(ii0 + t, Ni - 1) * LDY + jj0;
-    if (R == 3) {
-      const float2 L2 = lds2(row - 4);
-      const float r2x = row[4];
-      const float2 a01 = lds2(ay), a23 = lds2(ay + 2);
-      const float a4 = ay[4];
-      // faces b = j0-2, j0-1 | j0, j0+1 | j0+2
-      const float2 g01 = fma2(k27, sub2(shift2(L1, C), L1), sub2(shift2(L2, L1), C));
-      const float2 g23 = fma2(k27, sub2(shift2(C, R1), C), sub2(shift2(L1, C), R1));
-      const float g4 = (C.y - r2x) + 27.f * (R1.y - R1.x);
-      const float2 F01 = mul2(a01, g01), F23 = mul2(a23, g23);
-      const float F4 = a4 * g4;
-      const float2 hy = fma2(k27, sub2(F23, shift2(F01, F23)), sub2(F01, f2(F23.y, F4)));
-      H[t] = add2(H[t], hy);
+  return false;
+}
+
+}  // namespace
+
+bool res2d_make_plan(const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
+                     Res2dPlan* plan, std::string* why) {
+  const size_t budget = smem_bytes / sizeof(float);
+  const auto& V = variants();
+  plan->items.clear();
+  plan->groups.clear();
+  plan->smem = smem_bytes;
+  int i = 0;
+  while (i < n) {
+    int vi = -1, cs = 0;
+    if (!choose(boxes[i].N, R, interp_k, n_terms, budget, &vi, &cs)) {
+      *why = "a box of N = " + std::to_string(boxes[i].N) + " fits no cluster of at most " +
+             std::to_string(kResMaxCluster) + " CTAs";
+      return false;
+    }
+    int k = 1;
+    if (cs == 1) {
+      // pack consecutive boxes (sorted by size) served by the same instance
+      size_t floats = kResHeaderFloats;
+      int warps = 0;
+      k = 0;
+      while (i + k < n && k < kResMaxPack) {
+        const int N = boxes[i + k].N, Ni = N - 2 * R;
+        int vj = -1, csj = 0;
+        if (!choose(N, R, interp_k, n_terms, budget, &vj, &csj) || vj != vi || csj != 1) break;
+        const size_t f = res_offsets(geom(V[vi], N, Ni)).total;
+        const int w = (res_tiles(Ni, Ni) + 31) / 32;
+        if (k > 0 && (floats + f > budget || (warps + w) * 32 > kResThreads)) break;
+        floats += f;
+        warps += w;
+        ++k;
+      }
+    }
+    if (plan->groups.empty() || plan->groups.back().variant != vi || plan->groups.back().cs != cs)
+      plan->groups.push_back(Res2dGroup{cs, vi, (int)plan->items.size(), 0, 0});
+    plan->items.push_back(make_int2(i, k));
+    plan->groups.back().n_items++;
+    i += k;
+  }
+  return true;
+}
+
+static cudaLaunchConfig_t launch_config(const Res2dGroup& g, int grid, size_t smem, cudaStream_t st,
+                                        cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg = {};
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = g.cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kResThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = g.cs > 1 ? 1 : 0;
+  return cfg;
+}
+
+cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms) {
+  (void)radius;
+  const auto& V = variants();
+  for (Res2dGroup& g : plan->groups) {
+    const void* fn = reinterpret_cast<const void*>(V[g.variant].fn);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+    if (e != cudaSuccess) return e;
+    if (g.cs == 1) {
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResThreads, plan->smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      g.grid = std::min(g.n_items, per_sm * num_sms);
     } else {
-      const float2 a01 = lds2(ay);
-      const float a2 = ay[2];
-      const float2 g01 = sub2(C, shift2(L1, C));
-      const float g2 = R1.x - C.y;
-      const float2 F01 = mul2(a01, g01);
-      const float F2 = a2 * g2;
-      H[t] = add2(H[t], sub2(f2(F01.y, F2), F01));
+      cudaLaunchAttribute at[1];
+      cudaLaunchConfig_t cfg = launch_config(g, g.cs * num_sms, plan->smem, 0, at);
+      int clusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+      if (e != cudaSuccess) return e;
+      if (clusters < 1) return cudaErrorInvalidConfiguration;
+      g.grid = std::min(g.n_items, clusters) * g.cs;
     }
   }
+  return cudaSuccess;
 }
 
-// f = -m x H - alpha m x (m x H) for two nodes at once.
-__device__ __forceinline__ void ll_rhs2(const float2* m, const float2* H, float2 alpha, float2* f) {
-  const float2 p0 = sub2(mul2(m[1], H[2]), mul2(m[2], H[1]));
-  const float2 p1 = sub2(mul2(m[2], H[0]), mul2(m[0], H[2]));
-  const float2 p2 = sub2(mul2(m[0], H[1]), mul2(m[1], H[0]));
-  const float2 d0 = sub2(mul2(m[1], p2), mul2(m[2], p1));
-  const float2 d1 = sub2(mul2(m[2], p0), mul2(m[0], p2));
-  const float2 d2 = sub2(mul2(m[0], p1), mul2(m[1], p0));
-  const float2 mone = f2(-1.f, -1.f);
-  f[0] = mul2(fma2(alpha, d0, p0), mone);
-  f[1] = mul2(fma2(alpha, d1, p1), mone);
-  f[2] = mul2(fma2(alpha, d2, p2), mone);
+int res2d_max_grid(const Res2dPlan& plan) {
+  int g = 0;
+  for (const Res2dGroup& x : plan.groups) g = std::max(g, x.grid);
+  return g;
 }
 
-// Add w * (warp sum of part[0..2]) to the warp's Kahan accumulators in shared
-// memory (sum kah[c], compensation kah[3 + c]; the total is kah[c] - kah[3 + c]).
-// The product's rounding error e = w x - fl(w x) is exact (one fma) and goes into
-// the compensation. Explicit _rn intrinsics keep the compiler from contracting.
-__device__ __forceinline__ void warp_kahan_add(float* kah, int lane, float w, float* part) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) part[c] = warp_sum(part[c]);
-  if (lane == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float p = __fmul_rn(w, part[c]);
-      const float e = __fmaf_rn(w, part[c], -p);
-      const float s = kah[c], cmp = kah[3 + c];
-      const float y = __fsub_rn(p, cmp);
-      const float t = __fadd_rn(s, y);
-      kah[3 + c] = __fsub_rn(__fsub_rn(__fsub_rn(t, s), y), e);
-      kah[c] = t;
-    }
+cudaError_t res2d_launch(const MicroArgs& a, int radius, const Res2dPlan& plan, const int2* d_items,
+                         int* d_queues, cudaStream_t st) {
+  (void)radius;
+  const auto& V = variants();
+  for (size_t gi = 0; gi < plan.groups.size(); ++gi) {
+    const Res2dGroup& g = plan.groups[gi];
+    const ResLaunch L{d_items + g.first_item, g.n_items, d_queues + gi, g.cs};
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = launch_config(g, g.grid, plan.smem, st, at);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, V[g.variant].fn, a, L);
+    if (e != cudaSuccess) return e;
   }
-}
-
-template <int R, int TR>
-__global__ void __launch_bounds__(32 * ((kResMaxInterior + TR - 1) / TR))
-micro_fp32_2d_kernel(MicroArgs a) {
-  constexpr int D = 2;
-  extern __shared__ __align__(16) float fsm[];
-  __shared__ int s_box;
-  const int nmax = a.nmax;
-  const ResLayout Ly = res_layout(nmax, R);
-  const int LD = Ly.LD, LDI = Ly.LDI, LDY = Ly.LDY;
-  float* vA = fsm + Ly.vA;
-  float* vB = fsm + Ly.vB;
-  float* miS = fsm + Ly.mi;
-  float* hiS = fsm + Ly.hi;
-  float* hwS = fsm + Ly.hw;
-  float* afx = fsm + Ly.afx;
-  float* afy = fsm + Ly.afy;
-  double* red = reinterpret_cast<double*>(fsm + Ly.red);
-  const SetupSmem sm = carve_setup(reinterpret_cast<double*>(vB), D, nmax, a.interp_k, a.n_terms);
-  SetupSmem smr = sm;
-  smr.red = red;
-
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  float* kah = fsm + Ly.kah + 6 * warp;
-  const size_t cap = (size_t)nmax * nmax;
-  double* mi64 = reinterpret_cast<double*>(a.arena + (size_t)blockIdx.x * a.slot_bytes);
-  double* af64 = mi64 + 3 * cap;
-  const float am = (float)a.alpha_micro;
-  const float2 alpha2 = f2(am, am);
-
-  for (;;) {
-    const int b = next_box(a.queue, &s_box);
-    if (b >= a.n_boxes) break;
-    const BoxDesc bd = a.boxes[b];
-    const int N = bd.N, Ni = N - 2 * R;
-    const int ntot = N * N;
-    const Strides<D> st(N);
-    box_setup_tables<D>(a, bd, smr);
-
-    // ---- FP64 set-up through the arena: m_init (Section 4.1) and a^eps at the faces.
-    int bad = 0;
-    for (int idx = tid; idx < ntot; idx += nt) {
-      double P[3];
-      interp_P<D>(a, smr, N, idx, P);
-      const double inv = 1.0 / sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) mi64[c * cap + idx] = P[c] * inv;
-      int j[3];
-      node_coords<D>(idx, N, j);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        double v = 0.0;
-        if (j[k] < N - 1) {
-          v = face_coef<D>(a, smr, N, idx, k);
-          bad |= !(v > 0.0);
-        }
-        af64[k * cap + idx] = v;
-      }
-    }
-    if (bad) atomicOr(a.err, kErrCoefNonPositive);
-    if (tid < 6 * 32) fsm[Ly.kah + tid] = 0.f;
-    __syncthreads();   // the set-up tables (overlaying vB) are no longer needed
-
-    // ---- Shared-memory fields: v = 0, m_init, face coefficients, H(m_init), H(W).
-    for (int e = tid; e < 3 * nmax * LD; e += nt) {
-      vA[e] = 0.f;
-      vB[e] = 0.f;
-    }
-    const int f0 = R == 3 ? R - 2 : R - 1;     // first face row/column used by the stencil
-    const int nf = Ni + (R == 3 ? 3 : 1);
-    for (int e = tid; e < 3 * Ni * Ni; e += nt) {
-      const int c = e / (Ni * Ni), r = e - c * Ni * Ni;
-      const int ii = r / Ni, jj = r - ii * Ni;
-      miS[(c * Ni + ii) * LDI + jj] = (float)mi64[c * cap + (ii + R) * N + (jj + R)];
-    }
-    for (int e = tid; e < nf * Ni; e += nt) {
-      const int f = e / Ni, jj = e - f * Ni;
-      afx[f * LDI + jj] = (float)af64[(f + f0) * N + (jj + R)];        // x-face between rows f+f0, f+f0+1
-    }
-    for (int e = tid; e < Ni * nf; e += nt) {
-      const int ii = e / nf, g = e - ii * nf;
-      afy[ii * LDY + g] = (float)af64[cap + (ii + R) * N + (g + f0)];   // y-face between columns g+f0, g+f0+1
-    }
-    const double cs64 = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
-    const double* W1d = a.W64 + bd.wofs;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int e = tid; e < Ni * Ni; e += nt) {
-      const int ii = e / Ni, jj = e - ii * Ni;
-      const int idx = (ii + R) * N + (jj + R);
-      double H[3];
-      stencil_H<D, R, double>(mi64, af64, cap, st, idx, cs64, H);
-      const double W = W1d[ii + R] * W1d[jj + R];
-      s0 += W * H[0];
-      s1 += W * H[1];
-      s2 += W * H[2];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) hiS[(c * Ni + ii) * LDI + jj] = (float)H[c];
-      // H(W) with the same operator (W vanishes on and near the ring)
-      double hwd = 0.0;
-#pragma unroll 1
-      for (int k = 0; k < D; ++k) {
-        const int s = st.s[k];
-        const double* af = af64 + k * cap;
-        double Wv[7];
-#pragma unroll
-        for (int o = -R; o <= R; ++o) {
-          const int id = idx + o * s;
-          const int r_ = id / N, c_ = id - r_ * N;
-          Wv[o + R] = W1d[r_] * W1d[c_];
-        }
-        if (R == 1) {
-          hwd += af[idx] * (Wv[2] - Wv[1]) - af[idx - s] * (Wv[1] - Wv[0]);
-        } else {
-          const double g_2 = (Wv[0] - Wv[3]) + 27.0 * (Wv[2] - Wv[1]);
-          const double g_1 = (Wv[1] - Wv[4]) + 27.0 * (Wv[3] - Wv[2]);
-          const double g0 = (Wv[2] - Wv[5]) + 27.0 * (Wv[4] - Wv[3]);
-          const double g1 = (Wv[3] - Wv[6]) + 27.0 * (Wv[5] - Wv[4]);
-          hwd += (af[idx - 2 * s] * g_2 - af[idx + s] * g1) + 27.0 * (af[idx] * g0 - af[idx - s] * g_1);
-        }
-      }
-      hwS[ii * LDI + jj] = (float)(hwd * cs64);
-    }
-    {
-      double wsum = 0.0;
-      for (int n = 0; n <= a.msteps; ++n) wsum += a.w64[n];
-      s0 *= wsum;
-      s1 *= wsum;
-      s2 *= wsum;
-    }
-    __syncthreads();
-
-    // ---- Thread tile: rows i0 .. i0+TR-1, columns j0, j0+1.
-    const int ii0 = warp * TR;
-    const int i0 = R + ii0;
-    const int jj0 = 2 * lane;
-    const int j0 = R + jj0;
-    const bool tile_active = jj0 < Ni && ii0 < Ni;
-    const float2 cmask = f2(1.f, (jj0 + 1 < Ni) ? 1.f : 0.f);   // odd Ni: the second column is ring
-    const float csf = (float)cs64;
-    const float2 cs2 = f2(csf, csf);
-    const float dtf = (float)bd.dt;
-    const float2 dt2 = f2(dtf, dtf), hdt2 = f2(0.5f * dtf, 0.5f * dtf);
-    __nv_bfloat162 eB[3][TR], vlo[3][TR];
-#pragma unroll
-    for (int t = 0; t < TR; ++t)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        vlo[c][t] = __float2bfloat162_rn(0.f);
-        eB[c][t] = __float2bfloat162_rn(0.f);
-      }
-    const float2 half2 = f2(0.5f, 0.5f);
-
-    for (int n = 0; n < a.msteps; ++n) {
-      const float om = a.om32[n + 1];
-      if (tile_active) {
-        // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
-        float2 Hs[3][TR];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          tile_stencil<R, TR>(vA + c * nmax * LD, LD, N, i0, j0, afx, LDI, nf, jj0, afy, LDY, ii0, Ni, Hs[c]);
-#pragma unroll
-        for (int t = 0; t < TR; ++t) {
-          if (ii0 + t >= Ni) continue;
-          const int ro = (ii0 + t) * LDI + jj0;
-          float2 v[3], m[3], H[3], f[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            v[c] = lds2(vA + (c * nmax + i0 + t) * LD + j0 + 1);
-            m[c] = add2(lds2(miS + c * Ni * LDI + ro), v[c]);
-            H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * Ni * LDI + ro));
-          }
-          ll_rhs2(m, H, alpha2, f);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float2 delta = mul2(dt2, f[c]);
-            const float2 vb = add2(v[c], delta);
-            eB[c][t] = __float22bfloat162_rn(sub2(delta, sub2(vb, v[c])));
-            *reinterpret_cast<float2*>(vB + (c * nmax + i0 + t) * LD + j0 + 1) = mul2(vb, cmask);
-          }
-        }
-      }
-      __syncthreads();
-      float part[3] = {0.f, 0.f, 0.f};
-      if (tile_active) {
-        // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
-        float2 Hs[3][TR];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          tile_stencil<R, TR>(vB + c * nmax * LD, LD, N, i0, j0, afx, LDI, nf, jj0, afy, LDY, ii0, Ni, Hs[c]);
-#pragma unroll
-        for (int t = 0; t < TR; ++t) {
-          if (ii0 + t >= Ni) continue;
-          const int ro = (ii0 + t) * LDI + jj0;
-          float2 mi[3], m[3], H[3], k2[3], vh[3], d[3], vt[3], vbo[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            mi[c] = lds2(miS + c * Ni * LDI + ro);
-            vbo[c] = lds2(vB + (c * nmax + i0 + t) * LD + j0 + 1);
-            m[c] = add2(mi[c], vbo[c]);
-            H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * Ni * LDI + ro));
-          }
-          ll_rhs2(m, H, alpha2, k2);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            vh[c] = lds2(vA + (c * nmax + i0 + t) * LD + j0 + 1);
-            // dt/2 (k1 + k2) with dt k1 = (v_B - v) + e_B
-            d[c] = fma2(hdt2, k2[c], mul2(half2, add2(sub2(vbo[c], vh[c]), __bfloat1622float2(eB[c][t]))));
-            vt[c] = add2(vh[c], d[c]);
-          }
-          const float2 hw = lds2(hwS + ro);
-          // s = 2 m_init.vt + |vt|^2; c = -s / (sqrt(1+s)(1+sqrt(1+s)))
-          float2 sdot = mul2(mi[0], vt[0]);
-          sdot = fma2(mi[1], vt[1], sdot);
-          sdot = fma2(mi[2], vt[2], sdot);
-          float2 sq = mul2(vt[0], vt[0]);
-          sq = fma2(vt[1], vt[1], sq);
-          sq = fma2(vt[2], vt[2], sq);
-          const float2 s = fma2(f2(2.f, 2.f), sdot, sq);
-          const float r0 = rsqrtf(1.f + s.x), r1 = rsqrtf(1.f + s.y);
-          const float2 cf = f2(-s.x * r0 * r0 / (1.f + r0), -s.y * r1 * r1 / (1.f + r1));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float2 inc = add2(fma2(cf, add2(mi[c], vt[c]), d[c]), __bfloat1622float2(vlo[c][t]));
-            const float2 nh = add2(vh[c], inc);
-            vlo[c][t] = __float22bfloat162_rn(sub2(inc, sub2(nh, vh[c])));
-            const float2 nv = mul2(nh, cmask);
-            *reinterpret_cast<float2*>(vA + (c * nmax + i0 + t) * LD + j0 + 1) = nv;
-            // H(W) times the exact change of the stored state (zero in a ring column)
-            const float2 pr = mul2(hw, sub2(nv, vh[c]));
-            part[c] += pr.x + pr.y;
-          }
-        }
-      }
-      if (om != 0.f) warp_kahan_add(kah, lane, om, part);
-      __syncthreads();
-    }
-
-    double acc0 = s0, acc1 = s1, acc2 = s2;
-    if (lane == 0) {
-      acc0 += (double)kah[0] - (double)kah[3];
-      acc1 += (double)kah[1] - (double)kah[4];
-      acc2 += (double)kah[2] - (double)kah[5];
-    }
-    block_sum3(acc0, acc1, acc2, red);
-    if (tid == 0) {
-      a.Havg[bd.p] = acc0;
-      a.Havg[a.P + bd.p] = acc1;
-      a.Havg[2 * a.P + bd.p] = acc2;
-      if (!(isfinite(acc0) && isfinite(acc1) && isfinite(acc2))) atomicOr(a.err, kErrNonFinite);
-    }
-  }
-}
-
-constexpr int kResTR = 4;
-
-int res2d_block(int nmax, int R) {
-  const int ni = nmax - 2 * R;
-  return 32 * ((ni + kResTR - 1) / kResTR);
-}
-
-template <int R>
-static cudaError_t prepare_r(size_t smem, int* per_sm) {
-  auto kern = micro_fp32_2d_kernel<R, kResTR>;
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kern);
-  if (e != cudaSuccess) return e;
-  const int dyn_max = optin - (int)fa.sharedSizeBytes;
-  if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, 32 * ((kResMaxInterior + kResTR - 1) / kResTR), smem);
-}
-
-cudaError_t prepare_micro_fp32_2d(int radius, size_t smem, int* ctas_per_sm) {
-  return radius == 3 ? prepare_r<3>(smem, ctas_per_sm) : prepare_r<1>(smem, ctas_per_sm);
-}
-
-cudaError_t launch_micro_fp32_2d(const MicroArgs& a, int radius, int grid, int block, size_t smem,
-                                 cudaStream_t st) {
-  if (radius == 3) micro_fp32_2d_kernel<3, kResTR><<<grid, block, smem, st>>>(a);
-  else micro_fp32_2d_kernel<1, kResTR><<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,28 @@ def test_resident_2d_kernel_parity(torch_cuda, case):
     assert rel_err(Hg, Hr) < TOL[1], (case, rel_err(Hg, Hr))
 
 
+# Boxes too large for one CTA: split by rows over a thread-block cluster, with the
+# halo rows exchanged through distributed shared memory (canvas instances with
+# compile-time strides, and the instance with strides from the box).
+CLUSTER = {
+    "canvas_80_odd": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=75, micro_steps=30)),
+    "canvas_128": ("c5_sweep", dict(n_macro=(5, 5, 1), box_n=128, micro_steps=20)),
+    "box_strides_140": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=140, micro_steps=20)),
+    "box_strides_order2_101": ("c2_2d", dict(n_macro=(5, 6, 1), box_n=101, micro_steps=24, stencil_order=2)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CLUSTER))
+def test_resident_2d_kernel_clusters(torch_cuda, case):
+    name, over = CLUSTER[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, _ = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    pts = [0, 7, cfg.n_points - 1]
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
+
+
 def test_resident_2d_kernel_uneven_boxes(torch_cuda):
     cfg = _uneven_small()
     M0 = W.initial_field(cfg)
