@@ -34,10 +34,9 @@ ResDims geom(const ResVariant& v, int N, int Sa) {
 
 // A slab of Sa rows of a box of N nodes under geometry d fits one CTA: shared
 // memory (with the header), threads, and the set-up tables inside the vB region.
-bool slab_fits(const ResDims& d, int N, int R, int Sa, int interp_k, int n_terms, size_t budget_floats) {
-  const int Ni = N - 2 * R;
+bool slab_fits(const ResDims& d, int N, int Sa, int interp_k, int n_terms, size_t budget_floats) {
   return (size_t)res_offsets(d).total + kResHeaderFloats <= budget_floats &&
-         (res_tiles(Sa, Ni) + 31) / 32 * 32 <= kResThreads && res_setup_fits(d, N, interp_k, n_terms);
+         (res_tiles(Sa, d.CPp) + 31) / 32 * 32 <= kResThreads && res_setup_fits(d, N, interp_k, n_terms);
 }
 
 bool cluster_ok(int cs, int Sa, int Ni, int R) {
@@ -54,7 +53,7 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
     if (v.R != R || v.NC == 0 || v.NC < N) continue;
     const int Sa = (Ni + v.cs - 1) / v.cs;
     if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
-    if (!slab_fits(geom(v, N, Sa), N, R, Sa, interp_k, n_terms, budget)) continue;
+    if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
     *vi = i;
     *cs_out = v.cs;
     return true;
@@ -65,7 +64,7 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
     for (int cs = 1; cs <= kResMaxCluster; ++cs) {
       const int Sa = (Ni + cs - 1) / cs;
       if (!cluster_ok(cs, Sa, Ni, R)) continue;
-      if (!slab_fits(geom(v, N, Sa), N, R, Sa, interp_k, n_terms, budget)) continue;
+      if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
       *vi = i;
       *cs_out = cs;
       return true;
@@ -101,8 +100,9 @@ bool res2d_make_plan(const BoxDesc* boxes, int n, int R, int interp_k, int n_ter
         const int N = boxes[i + k].N, Ni = N - 2 * R;
         int vj = -1, csj = 0;
         if (!choose(N, R, interp_k, n_terms, budget, &vj, &csj) || vj != vi || csj != 1) break;
-        const size_t f = res_offsets(geom(V[vi], N, Ni)).total;
-        const int w = (res_tiles(Ni, Ni) + 31) / 32;
+        const ResDims dq = geom(V[vi], N, Ni);
+        const size_t f = res_offsets(dq).total;
+        const int w = (res_tiles(Ni, dq.CPp) + 31) / 32;
         if (k > 0 && (floats + f > budget || (warps + w) * 32 > kResThreads)) break;
         floats += f;
         warps += w;

@@ -54,14 +54,38 @@ constexpr int kResThreads = 512;     // threads per CTA (16 warps, 128 registers
 constexpr int kResMaxPack = 8;       // boxes per work item
 constexpr int kResMaxCluster = 8;    // CTAs per cluster (portable limit)
 
+// Thread tiles of a box (TR rows x 2 columns) are numbered row-major, CPp tiles
+// per row group: the column pairs (Ni + 1)/2 padded to 16 (two row groups per warp,
+// one per half-warp), to 32 (one per warp) or to a multiple of 4. In the last case
+// row groups share half-warps, and every row stride is chosen congruent to CPp/2
+// mod 8 floats: then TR * stride = 2 CPp mod 32 and tile t reads its float2 at bank
+// 2t + const mod 32, so the 16 lanes of a half-warp (one 64-bit wavefront) never
+// share a bank.
+__host__ __device__ inline int res_cp_pad(int Ni) {
+  const int CP = (Ni + 1) / 2;
+  if (CP <= 16) return 16;
+  if (CP > 28 && CP <= 32) return 32;
+  return (CP + 3) & ~3;
+}
+
+// The smallest even stride >= minimum that keeps the tiles' accesses conflict-free.
+__host__ __device__ inline int res_stride(int minimum, int CPp) {
+  if (CPp == 16 || CPp == 32) return (minimum + 1) & ~1;
+  const int r = (CPp / 2) & 7;
+  int s = minimum;
+  while ((s & 7) != r) ++s;
+  return s;
+}
+
 // Dimensions of one slab: interior rows [r0, r0 + S) of a box of N nodes per axis.
 struct ResDims {
   int N, Ni, S;
   int rows;   // rows of vA/vB: S + 2r (halo or ring rows on both sides)
   int LD;     // row stride of vA/vB (column j at offset j + 1; columns up to N + 2 readable)
-  int LDI;    // row stride of the interior arrays (>= Ni + 1)
+  int LDI;    // row stride of the interior arrays (>= Ni)
   int nf;     // face rows of the x-face array, S + 3 (order 4) or S + 1 (order 2)
   int LDY;    // row stride of the y-face array (>= Ni + 4 or Ni + 2)
+  int CPp;    // tiles per row group
 };
 
 __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
@@ -70,10 +94,11 @@ __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
   d.Ni = N - 2 * R;
   d.S = S;
   d.rows = S + 2 * R;
-  d.LD = (N + 5) & ~1;
-  d.LDI = (d.Ni + 1) & ~1;
+  d.CPp = res_cp_pad(d.Ni);
+  d.LD = res_stride(N + 4, d.CPp);
+  d.LDI = res_stride(d.Ni, d.CPp);
   d.nf = S + (R == 3 ? 3 : 1);
-  d.LDY = (d.Ni + (R == 3 ? 3 : 1) + 2) & ~1;
+  d.LDY = res_stride(d.Ni + (R == 3 ? 4 : 2), d.CPp);
   return d;
 }
 
@@ -121,7 +146,8 @@ constexpr int kResCsumDoubles = 4 * kResMaxCluster;
 constexpr int kResHeaderFloats =
     ((2 * (kResRedDoubles + kResCsumDoubles) + (int)(kResMaxPack * sizeof(PackBox) / 4) + 6 * (kResThreads / 32)) + 3) & ~3;
 
-__host__ __device__ inline int res_tiles(int S, int Ni) { return ((S + kResTR - 1) / kResTR) * ((Ni + 1) / 2); }
+// Tiles (threads) of a slab of S rows with CPp tiles per row group.
+__host__ __device__ inline int res_tiles(int S, int CPp) { return ((S + kResTR - 1) / kResTR) * CPp; }
 
 // Set-up tables (FP64) overlay the slab's vB region while the slab is being set up.
 __host__ __device__ inline bool res_setup_fits(const ResDims& d, int N, int interp_k, int n_terms) {
@@ -340,9 +366,10 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         p.Sa = Sa;
         p.base = o;
         p.warp0 = w0;
-        p.nwarps = (res_tiles(S, Ni) + 31) / 32;
+        const ResDims dq = res_geom<R, NC, SAC>(Ni + 2 * R, Sa);
+        p.nwarps = (res_tiles(S, dq.CPp) + 31) / 32;
         w0 += p.nwarps;
-        o += res_offsets(res_geom<R, NC, SAC>(Ni + 2 * R, Sa)).total;
+        o += res_offsets(dq).total;
       }
     }
     if (tid < 6 * (kResThreads / 32)) kahA[tid] = 0.f;
@@ -476,10 +503,9 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       Ni = bd.N - 2 * R;
       obase = p.base;
       const int t = (warp - p.warp0) * 32 + lane;
-      const int CP = (Ni + 1) / 2;
-      ii0 = (t / CP) * TR;          // row within the slab
-      jj0 = 2 * (t % CP);
-      active = t < res_tiles(S, Ni);
+      ii0 = (t / d.CPp) * TR;          // row within the slab
+      jj0 = 2 * (t % d.CPp);
+      active = t < res_tiles(S, d.CPp) && jj0 < Ni;
       dtf = (float)bd.dt;
       csf = (float)(R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx));
     }

@@ -8,7 +8,7 @@ int res2d_variants_cluster_a(const ResVariant** v) {
   static const ResVariant t[] = {
       {3, 72, 33, 2, micro_fp32_2d_kernel<3, kResTR, 72, 33>},
       {3, 80, 37, 2, micro_fp32_2d_kernel<3, kResTR, 80, 37>},
-      {3, 88, 41, 2, micro_fp32_2d_kernel<3, kResTR, 88, 41>},
+      {3, 88, 28, 3, micro_fp32_2d_kernel<3, kResTR, 88, 28>},
       {3, 96, 30, 3, micro_fp32_2d_kernel<3, kResTR, 96, 30>},
   };
   *v = t;
