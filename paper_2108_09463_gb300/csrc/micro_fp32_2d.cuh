@@ -251,16 +251,18 @@ __device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD
 
 // f = -m x H - alpha m x (m x H) for two nodes at once.
 __device__ __forceinline__ void ll_rhs2(const float2* m, const float2* H, float2 alpha, float2* f) {
-  const float2 p0 = sub2(mul2(m[1], H[2]), mul2(m[2], H[1]));
-  const float2 p1 = sub2(mul2(m[2], H[0]), mul2(m[0], H[2]));
-  const float2 p2 = sub2(mul2(m[0], H[1]), mul2(m[1], H[0]));
-  const float2 d0 = sub2(mul2(m[1], p2), mul2(m[2], p1));
-  const float2 d1 = sub2(mul2(m[2], p0), mul2(m[0], p2));
-  const float2 d2 = sub2(mul2(m[0], p1), mul2(m[1], p0));
-  const float2 mone = f2(-1.f, -1.f);
-  f[0] = mul2(fma2(alpha, d0, p0), mone);
-  f[1] = mul2(fma2(alpha, d1, p1), mone);
-  f[2] = mul2(fma2(alpha, d2, p2), mone);
+  // f = q + alpha m x q with q = H x m = -m x H (so m x q = -m x (m x H)); the cross
+  // products as one product and one fma each, the sign in the negated m.
+  const float2 n0 = f2(-m[0].x, -m[0].y), n1 = f2(-m[1].x, -m[1].y), n2 = f2(-m[2].x, -m[2].y);
+  const float2 q0 = fma2(H[1], m[2], mul2(H[2], n1));
+  const float2 q1 = fma2(H[2], m[0], mul2(H[0], n2));
+  const float2 q2 = fma2(H[0], m[1], mul2(H[1], n0));
+  const float2 d0 = fma2(m[1], q2, mul2(n2, q1));
+  const float2 d1 = fma2(m[2], q0, mul2(n0, q2));
+  const float2 d2 = fma2(m[0], q1, mul2(n1, q0));
+  f[0] = fma2(alpha, d0, q0);
+  f[1] = fma2(alpha, d1, q1);
+  f[2] = fma2(alpha, d2, q2);
 }
 
 // Add w * (warp sum of part[0..2]) to the warp's Kahan accumulators in shared
@@ -608,8 +610,9 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
           sq = fma2(vt[1], vt[1], sq);
           sq = fma2(vt[2], vt[2], sq);
           const float2 s = fma2(f2(2.f, 2.f), sdot, sq);
+          // (c is a small correction, so the approximate quotient costs nothing measurable)
           const float rr0 = rsqrtf(1.f + s.x), rr1 = rsqrtf(1.f + s.y);
-          const float2 cf = f2(-s.x * rr0 * rr0 / (1.f + rr0), -s.y * rr1 * rr1 / (1.f + rr1));
+          const float2 cf = f2(__fdividef(-s.x * rr0 * rr0, 1.f + rr0), __fdividef(-s.y * rr1 * rr1, 1.f + rr1));
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const float2 inc = add2(fma2(cf, add2(mi[c], vt[c]), dd[c]), __bfloat1622float2(vlo[c][t]));
