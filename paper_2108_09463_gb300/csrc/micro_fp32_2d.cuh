@@ -559,9 +559,9 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
           ll_rhs2(m, H, alpha2, f);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const float2 delta = mul2(dt2, f[c]);
-            float2 vb = add2(v[c], delta);
-            eB[c][t] = __float22bfloat162_rn(sub2(delta, sub2(vb, v[c])));
+            float2 vb = fma2(dt2, f[c], v[c]);
+            // e_B / 2 = (v + dt k1 - v_B) / 2 (v_B - v is exact): stage 2 adds it to (v_B - v) / 2
+            eB[c][t] = __float22bfloat162_rn(fma2(hdt2, f[c], mul2(half2, sub2(v[c], vb))));
             if (!col2) vb.y = 0.f;
             *reinterpret_cast<float2*>(vB + c * cstrV + vo) = vb;
           }
@@ -572,7 +572,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         push_halo<R, NC, SAC>(a, fsm, pk, 1, rank, cs);
         cg::this_cluster().sync();
       }
-      float part[3] = {0.f, 0.f, 0.f};
+      float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
       if (active) {
         // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
         float2 Hs[3][TR];
@@ -598,7 +598,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
           for (int c = 0; c < 3; ++c) {
             vh[c] = lds2(vA + c * cstrV + vo);
             // dt/2 (k1 + k2) with dt k1 = (v_B - v) + e_B
-            dd[c] = fma2(hdt2, k2[c], mul2(half2, add2(sub2(vbo[c], vh[c]), __bfloat1622float2(eB[c][t]))));
+            dd[c] = fma2(hdt2, k2[c], fma2(half2, sub2(vbo[c], vh[c]), __bfloat1622float2(eB[c][t])));
             vt[c] = add2(vh[c], dd[c]);
           }
           const float2 hw = lds2(hwS + ro);
@@ -621,12 +621,14 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
             if (!col2) nh.y = 0.f;
             *reinterpret_cast<float2*>(vA + c * cstrV + vo) = nh;
             // H(W) times the exact change of the stored state (zero in a ring column)
-            const float2 pr = mul2(hw, sub2(nh, vh[c]));
-            part[c] += pr.x + pr.y;
+            part2[c] = fma2(hw, sub2(nh, vh[c]), part2[c]);
           }
         }
       }
-      if (om != 0.f) warp_kahan_add(kah, lane, om, part);
+      if (om != 0.f) {
+        float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};
+        warp_kahan_add(kah, lane, om, part);
+      }
       __syncthreads();
       if (cs > 1) {
         push_halo<R, NC, SAC>(a, fsm, pk, 0, rank, cs);
