@@ -92,9 +92,11 @@ typedef struct {
   int interp_order;             /* 2k in {2, 4}; <= 0: 4                           */
   int stencil_order;            /* 2 or 4; <= 0: 4                                 */
   int precision;                /* hmm_precision                                   */
-  int kernel_variant;           /* HMM_FP32_BATCHED kernel: 0 automatic (resident
-                                   2D kernel when d = 2 and N - 2r <= 64, else the
-                                   generic arena kernel), 1 generic, 2 resident    */
+  int kernel_variant;           /* HMM_FP32_BATCHED kernel: 0 automatic (the
+                                   shared-memory-resident kernels when every box
+                                   fits them: d = 2, N up to the 8-CTA cluster
+                                   limit; d = 3, order 4, N <= 32; else the generic
+                                   arena kernel), 1 generic, 2 resident            */
   int reserved[4];              /* must be zero                                    */
 } hmm_params;
 
@@ -160,7 +162,7 @@ hmm_status hmm_macro_dt(void* handle, double* dt_macro);
  * another framework's memory pool (so cudaMalloc fails), and latency-critical
  * paths that cannot afford cudaMalloc/cudaFree, which may synchronise the device.
  * It takes the problem directly (no handle), runs the same batched FP32 micro
- * solve as hmm_micro_batch with kernel_variant 0/1, and calls no cudaMalloc,
+ * solve as hmm_micro_batch with kernel_variant 1, and calls no cudaMalloc,
  * cudaFree or other allocating routine: every buffer it needs (box table,
  * weight tables, work counter, error word, per-CTA arenas) is carved out of one
  * fixed device array of 32 MiB inside the library, reserved on every GPU that

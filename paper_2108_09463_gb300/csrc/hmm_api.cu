@@ -496,9 +496,9 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  std::string why = "the resident kernel needs the FP32 form and d = 2";
-  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim == 2 &&
-                      res2d_make_plan(h->boxes.data(), h->P, h->radius, h->interp_k, p.n_terms,
+  std::string why = "the resident kernels need the FP32 form and d = 2 or 3";
+  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 &&
+                      res2d_make_plan(h->dim, h->boxes.data(), h->P, h->radius, h->interp_k, p.n_terms,
                                       (size_t)optin - 256, &h->plan, &why) &&
                       (int)h->plan.groups.size() <= kQueues;
   if (p.kernel_variant == 2 && !res_ok) return fail(h, HMM_ERR_INVALID_ARG, why.c_str());
@@ -508,7 +508,7 @@ hmm_status build(HmmHandle* h) {
   int per_sm = 0;
   if (h->res2d) {
     HMM_CUDA(h, res2d_prepare(h->radius, &h->plan, h->num_sms));
-    h->slot_bytes = res2d_slot_bytes(h->nmax);
+    h->slot_bytes = h->dim == 3 ? res3d_slot_bytes(h->nmax) : res2d_slot_bytes(h->nmax);
     HMM_CUDA(h, cudaMalloc(&h->d_items, sizeof(int2) * h->plan.items.size()));
     HMM_CUDA(h, cudaMemcpy(h->d_items, h->plan.items.data(), sizeof(int2) * h->plan.items.size(),
                            cudaMemcpyHostToDevice));

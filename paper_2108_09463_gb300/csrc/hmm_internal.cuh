@@ -90,13 +90,15 @@ struct Res2dPlan {
   std::vector<int2> items;
   std::vector<Res2dGroup> groups;
   size_t smem = 0;  // dynamic shared memory per CTA
+  int dim = 2;      // 2: micro_fp32_2d_kernel instances, 3: micro_fp32_3d_kernel instances
 };
 // False (with the reason) when some box fits no cluster of the portable size.
-bool res2d_make_plan(const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
+bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
                      Res2dPlan* plan, std::string* why);
 cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms);
 int res2d_max_grid(const Res2dPlan& plan);
 size_t res2d_slot_bytes(int nmax);
+size_t res3d_slot_bytes(int nmax);
 cudaError_t res2d_launch(const MicroArgs& a, int radius, const Res2dPlan& plan, const int2* d_items,
                          int* d_queues, cudaStream_t st);
 

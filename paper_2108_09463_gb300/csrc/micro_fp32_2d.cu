@@ -5,16 +5,17 @@
 #include <string>
 #include <vector>
 
-#include "micro_fp32_2d.cuh"
+#include "micro_fp32_3d.cuh"
 
 namespace hmm {
 
 size_t res2d_slot_bytes(int nmax) { return (res2d_arena_doubles(nmax) * 8 + 255) & ~(size_t)255; }
+size_t res3d_slot_bytes(int nmax) { return (res3d_arena_doubles(nmax) * 8 + 255) & ~(size_t)255; }
 
 namespace {
 
-const std::vector<ResVariant>& variants() {
-  static const std::vector<ResVariant> all = [] {
+const std::vector<ResVariant>& variants(int dim) {
+  static const std::vector<ResVariant> all2 = [] {
     std::vector<ResVariant> v;
     int (*getters[])(const ResVariant**) = {res2d_variants_pack, res2d_variants_cluster_a,
                                             res2d_variants_cluster_b, res2d_variants_any};
@@ -25,7 +26,32 @@ const std::vector<ResVariant>& variants() {
     }
     return v;
   }();
-  return all;
+  static const std::vector<ResVariant> all3 = [] {
+    const ResVariant* t = nullptr;
+    const int n = res3d_variants(&t);
+    return std::vector<ResVariant>(t, t + n);
+  }();
+  return dim == 3 ? all3 : all2;
+}
+
+// 3D: the first canvas that holds the box (its cluster size is fixed), if its slabs fit.
+bool choose3(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out) {
+  const auto& V = variants(3);
+  const int Ni = N - 2 * R;
+  for (int i = 0; i < (int)V.size(); ++i) {
+    const ResVariant& v = V[i];
+    if (v.R != R || v.NC < N || v.cs > Ni) continue;
+    const int Sa = (Ni + v.cs - 1) / v.cs;
+    if (Sa > v.SAC) continue;
+    const Res3Dims d = res3_dims(v.NC, R, v.SAC);
+    if ((size_t)res3_offsets(d).total + kResHeaderFloats > budget) continue;
+    if ((res3_tiles(Sa, Ni, d.CPp, v.TZ) + 31) / 32 * 32 > kResThreads) continue;
+    if (setup_smem_doubles(3, N, interp_k, n_terms) * 2 > (size_t)3 * d.Sc * d.PV) continue;
+    *vi = i;
+    *cs_out = v.cs;
+    return true;
+  }
+  return false;
 }
 
 ResDims geom(const ResVariant& v, int N, int Sa) {
@@ -46,7 +72,7 @@ bool cluster_ok(int cs, int Sa, int Ni, int R) {
 // The instance and cluster size for a box: the first canvas (table order: growing
 // canvases) that holds it, else the box-stride instance with the smallest cluster.
 bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out) {
-  const auto& V = variants();
+  const auto& V = variants(2);
   const int Ni = N - 2 * R;
   for (int i = 0; i < (int)V.size(); ++i) {
     const ResVariant& v = V[i];
@@ -75,16 +101,29 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
 
 }  // namespace
 
-bool res2d_make_plan(const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
+bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
                      Res2dPlan* plan, std::string* why) {
   const size_t budget = smem_bytes / sizeof(float);
-  const auto& V = variants();
+  const auto& V = variants(2);
   plan->items.clear();
   plan->groups.clear();
   plan->smem = smem_bytes;
+  plan->dim = dim;
   int i = 0;
   while (i < n) {
     int vi = -1, cs = 0;
+    if (dim == 3) {
+      if (!choose3(boxes[i].N, R, interp_k, n_terms, budget, &vi, &cs)) {
+        *why = "no 3D resident instance holds a box of N = " + std::to_string(boxes[i].N) + " with this stencil";
+        return false;
+      }
+      if (plan->groups.empty() || plan->groups.back().variant != vi)
+        plan->groups.push_back(Res2dGroup{cs, vi, (int)plan->items.size(), 0, 0});
+      plan->items.push_back(make_int2(i, 1));
+      plan->groups.back().n_items++;
+      ++i;
+      continue;
+    }
     if (!choose(boxes[i].N, R, interp_k, n_terms, budget, &vi, &cs)) {
       *why = "a box of N = " + std::to_string(boxes[i].N) + " fits no cluster of at most " +
              std::to_string(kResMaxCluster) + " CTAs";
@@ -136,11 +175,15 @@ static cudaLaunchConfig_t launch_config(const Res2dGroup& g, int grid, size_t sm
 
 cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms) {
   (void)radius;
-  const auto& V = variants();
+  const auto& V = variants(plan->dim);
   for (Res2dGroup& g : plan->groups) {
     const void* fn = reinterpret_cast<const void*>(V[g.variant].fn);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
     if (e != cudaSuccess) return e;
+    if (g.cs > 8) {   // clusters beyond the portable size of 8
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
     if (g.cs == 1) {
       int per_sm = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResThreads, plan->smem);
@@ -169,7 +212,7 @@ int res2d_max_grid(const Res2dPlan& plan) {
 cudaError_t res2d_launch(const MicroArgs& a, int radius, const Res2dPlan& plan, const int2* d_items,
                          int* d_queues, cudaStream_t st) {
   (void)radius;
-  const auto& V = variants();
+  const auto& V = variants(plan.dim);
   for (size_t gi = 0; gi < plan.groups.size(); ++gi) {
     const Res2dGroup& g = plan.groups[gi];
     const ResLaunch L{d_items + g.first_item, g.n_items, d_queues + gi, g.cs};

@@ -680,6 +680,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
 struct ResVariant {
   int R, NC, SAC, cs;
   void (*fn)(MicroArgs, ResLaunch);
+  int TZ;   // 3D: planes per thread tile (0 for 2D)
 };
 
 int res2d_variants_pack(const ResVariant** v);

@@ -154,6 +154,26 @@ def test_resident_2d_kernel_clusters(torch_cuda, case):
     assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
 
 
+# 3D boxes: each split by z-planes over a cluster (planes beyond a CTA's slab read from
+# the neighbouring CTAs' shared memory), or held by one CTA when small.
+RESIDENT_3D = {
+    "n32_cluster7": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=32, micro_steps=20)),
+    "n21_cluster3_odd": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=21, mu_over_eps=0.9, micro_steps=24)),
+    "n16_one_cta": ("c4_3d", dict(n_macro=(5, 6, 5), box_n=16, mu_over_eps=0.9, micro_steps=30)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RESIDENT_3D))
+def test_resident_3d_kernel(torch_cuda, case):
+    name, over = RESIDENT_3D[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, _ = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    pts = [0, 11, cfg.n_points - 1]
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
+
+
 def test_resident_2d_kernel_uneven_boxes(torch_cuda):
     cfg = _uneven_small()
     M0 = W.initial_field(cfg)
