@@ -154,7 +154,12 @@ __device__ __forceinline__ float2 ld_cluster2(unsigned addr) {
 
 constexpr unsigned kRes3Ring = 0xffffffffu;   // table entry of a ring plane (zero)
 
-// z direction for one component over the tile's TZ planes: a rolling window over the
+// Split cluster barrier: arrive (release: this thread's shared-memory writes become
+// visible to the cluster) and wait (acquire). Executed by every thread of every CTA.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// z direction for one component over the tile's TZ planes, added to H: a rolling window over the
 // planes zl = z0-r .. z0+TZ+r-1 of the slab (local planes from this CTA's shared
 // memory; planes of the neighbouring slabs through the table rtab, indexed by zl + r,
 // of their shared::cluster addresses (component 0, row 0); ring planes zero) and over
@@ -179,7 +184,7 @@ __device__ __forceinline__ void zpass(const float* __restrict__ Vc, int coff, in
     for (int f = 0; f < TZ + 3; ++f) {
       const float2 p3 = ld(f + 3);
       const float2 F = mul2(fz(f), fma2(k27, sub2(p2, p1), sub2(p0, p3)));
-      if (f >= 3) H[f - 3] = fma2(k27, sub2(Fc, Fb), sub2(Fa, F));
+      if (f >= 3) H[f - 3] = add2(H[f - 3], fma2(k27, sub2(Fc, Fb), sub2(Fa, F)));
       Fa = Fb;
       Fb = Fc;
       Fc = F;
@@ -193,7 +198,7 @@ __device__ __forceinline__ void zpass(const float* __restrict__ Vc, int coff, in
     for (int f = 0; f < TZ + 1; ++f) {
       const float2 p1 = ld(f + 1);
       const float2 F = mul2(fz(f), sub2(p1, p0));
-      if (f >= 1) H[f - 1] = sub2(F, Fa);
+      if (f >= 1) H[f - 1] = add2(H[f - 1], sub2(F, Fa));
       Fa = F;
       p0 = p1;
     }
@@ -385,8 +390,8 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
       rtab[tid] = e;
     }
     __syncthreads();
-    // The neighbouring CTAs read this CTA's planes from stage 1 on.
-    if (cs > 1) cg::this_cluster().sync();
+    // The neighbouring CTAs read this CTA's planes from stage 1 on (after their wait).
+    if (cs > 1) cluster_arrive();
 
     // ---- This thread's tile: planes z0 .. z0+TZ-1 of the slab, row y, columns jj0, jj0+1.
     const int LD = d.LD, LDI = d.LDI, LDY = d.LDY, PV = d.PV, PI = d.PI, PY = d.PY, PFY = d.PFY;
@@ -423,19 +428,24 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
 
     for (int n = 0; n < a.msteps; ++n) {
       const float om = a.om32[n + 1];
+      // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1. The y and x
+      // directions read only this CTA's planes; the z direction waits for the cluster.
+      float2 Hs[3][TZ];
       if (active) {
-        // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
-        float2 Hs[3][TZ];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          zpass<R, TZ>(vA + c * cstrV, c * cstrV, PV, rowoff, z0, S, rtab, fzS, nfz, PI, Hs[c]);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int k = 0; k < TZ; ++k) {
             const int zl = min(z0 + k, S - 1);
             const float* P = vA + c * cstrV + zl * PV + rowoff;
-            Hs[c][k] = add2(Hs[c][k], add2(ypass<R>(P, LD, fyS + zl * PFY, LDI), xpass<R>(P, fxS + zl * PY)));
+            Hs[c][k] = add2(ypass<R>(P, LD, fyS + zl * PFY, LDI), xpass<R>(P, fxS + zl * PY));
           }
-        }
+      }
+      if (cs > 1) cluster_wait();
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          zpass<R, TZ>(vA + c * cstrV, c * cstrV, PV, rowoff, z0, S, rtab, fzS, nfz, PI, Hs[c]);
 #pragma unroll
         for (int k = 0; k < TZ; ++k) {
           const int zl = z0 + k;
@@ -459,22 +469,25 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
           }
         }
       }
-      if (cs > 1) cg::this_cluster().sync();
-      else __syncthreads();
+      __syncthreads();
+      if (cs > 1) cluster_arrive();
+      // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
       float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
       if (active) {
-        // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
-        float2 Hs[3][TZ];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          zpass<R, TZ>(vB + c * cstrV, c * cstrV, PV, rowoff, z0, S, rtab + ntab, fzS, nfz, PI, Hs[c]);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int k = 0; k < TZ; ++k) {
             const int zl = min(z0 + k, S - 1);
             const float* P = vB + c * cstrV + zl * PV + rowoff;
-            Hs[c][k] = add2(Hs[c][k], add2(ypass<R>(P, LD, fyS + zl * PFY, LDI), xpass<R>(P, fxS + zl * PY)));
+            Hs[c][k] = add2(ypass<R>(P, LD, fyS + zl * PFY, LDI), xpass<R>(P, fxS + zl * PY));
           }
-        }
+      }
+      if (cs > 1) cluster_wait();
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          zpass<R, TZ>(vB + c * cstrV, c * cstrV, PV, rowoff, z0, S, rtab + ntab, fzS, nfz, PI, Hs[c]);
 #pragma unroll
         for (int k = 0; k < TZ; ++k) {
           const int zl = z0 + k;
@@ -521,9 +534,10 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};
         warp_kahan_add(kah, lane, om, part);
       }
-      if (cs > 1) cg::this_cluster().sync();
-      else __syncthreads();
+      __syncthreads();
+      if (cs > 1) cluster_arrive();
     }
+    if (cs > 1) cluster_wait();   // pairs the last arrive
 
     // ---- H_avg: s0 plus the warps' Kahan sums; the slabs are added in rank order on rank 0.
     __syncthreads();
