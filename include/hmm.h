@@ -50,6 +50,15 @@ typedef enum {
   HMM_FP32_BATCHED = 1   /* FP32 perturbation-form micro state, FP64 averages */
 } hmm_precision;
 
+/* Time integrator of the micro problems (Section 3.1): HeunP, the paper's choice
+ * with artificial damping (Section 3.4), or RK4P, whose stability region holds
+ * part of the imaginary axis and which is cheaper per unit of micro time for
+ * small micro damping (Section 3.2). */
+typedef enum {
+  HMM_HEUNP = 0,
+  HMM_RK4P = 1
+} hmm_micro_stepper;
+
 /* One term of the material coefficient (Section 2.1 (A1); the examples of
  * Section 2.4 and Section 5 are sums of such terms):
  *     amp * prod_{k<d} g_k(2*pi*omega[k]*s_k + phase[k]),
@@ -86,7 +95,7 @@ typedef struct {
   double pts_per_eps;           /* K: micro grid spacing dx = eps_i/K              */
   double mu_over_eps;           /* mu/eps; <= 0: mu = 0.8*mu', mu' = (N-1)dx/2     */
   int micro_steps;              /* M micro time steps (eta = M*dt_micro)           */
-  double dt_safety;             /* dt_micro as a fraction of the HeunP stability
+  double dt_safety;             /* dt_micro as a fraction of the stepper's stability
                                    limit (eq. Cstab); <= 0: 0.8                    */
   int px, qx, pt, qt;           /* kernel parameters; <= 0: 3, 7, 3, 7             */
   int interp_order;             /* 2k in {2, 4}; <= 0: 4                           */
@@ -97,7 +106,9 @@ typedef struct {
                                    fits them: d = 2, N up to the 8-CTA cluster
                                    limit; d = 3, order 4, N <= 32; else the generic
                                    arena kernel), 1 generic, 2 resident            */
-  int reserved[4];              /* must be zero                                    */
+  int micro_stepper;            /* hmm_micro_stepper; RK4P runs on the generic
+                                   kernels (kernel_variant 0 selects them)         */
+  int reserved[3];              /* must be zero                                    */
 } hmm_params;
 
 /* Set-up (host only, plus device allocations on the current device).
@@ -107,7 +118,8 @@ typedef struct {
  * the averaging box [-mu, mu]^d stays inside the interior (off the Dirichlet
  * ring of width r = 1 or 3). Computes the smoothing kernels, the quadrature
  * weight tables, the micro time step of each box (dt = dt_safety *
- * s_max(alpha_micro) dx^2 / (a_max d lambda_s)), sorts the boxes by cost
+ * s_max(alpha_micro) dx^2 / (a_max d lambda_s), s_max the stability limit of the
+ * micro stepper on the ray (-alpha_micro + i) R+), sorts the boxes by cost
  * (longest first) and allocates the per-CTA arenas.
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
  * On success *handle_out owns all library memory until hmm_destroy. */

@@ -155,18 +155,27 @@ def time_weights(M: int, p: int, q: int, dtype=np.float64) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 
-def heun_stability_limit(alpha: float) -> float:
-    """Largest s > 0 with |1 + z + z^2/2| <= 1 for z = s(-alpha + i).
+def _amplification(stepper: int):
+    """Stability polynomial of the stepper: HeunP (0) 1 + z + z^2/2, RK4P (1) its
+    continuation to z^4/24 (Section 3.2, the related Runge-Kutta methods)."""
+    if stepper == 0:
+        return lambda z: 1.0 + z + 0.5 * z * z
+    if stepper == 1:
+        return lambda z: 1.0 + z * (1.0 + z * (0.5 + z * (1.0 / 6.0 + z / 24.0)))
+    raise ValueError("micro_stepper must be 0 (HeunP) or 1 (RK4P)")
 
-    The linearised LL Jacobian has eigenvalues (+-i - alpha) omega (Section 3.2);
-    Heun's amplification factor is 1 + z + z^2/2. Scans outward from s = 0 and
-    bisects the first exit from the unit disc.
+
+def stability_limit(alpha: float, stepper: int = 0) -> float:
+    """Largest s > 0 with |R(z)| <= 1 for z = s(-alpha + i), R the stepper's polynomial.
+
+    The linearised LL Jacobian has eigenvalues (+-i - alpha) omega (Section 3.2).
+    Scans outward from s = 0 and bisects the first exit from the unit disc.
     """
     w = complex(-alpha, 1.0)
+    R = _amplification(stepper)
 
     def amp(s):
-        z = s * w
-        return abs(1.0 + z + 0.5 * z * z)
+        return abs(R(s * w))
 
     s, ds = 0.0, 1e-3
     while amp(s + ds) <= 1.0:
@@ -183,6 +192,11 @@ def heun_stability_limit(alpha: float) -> float:
     return lo
 
 
+def heun_stability_limit(alpha: float) -> float:
+    """Largest s > 0 with |1 + z + z^2/2| <= 1 for z = s(-alpha + i) (HeunP)."""
+    return stability_limit(alpha, 0)
+
+
 def stencil_symbol_max(order: int) -> float:
     """max over theta of the squared symbol of the staggered D_s D_s (times dx^2).
 
@@ -196,14 +210,15 @@ def coef_upper_bound(cfg) -> float:
 
 
 def micro_dt(cfg, dx: float) -> float:
-    """Micro time step dt = safety * s_max(alpha_micro) / omega_max (reading G4).
+    """Micro time step dt = safety * s_max(alpha_micro) / omega_max (reading G4), s_max
+    the stability limit of the micro stepper (HeunP or RK4P).
 
     omega_max = a_max * d * lambda_s / dx^2 bounds the spectral radius of
     -div(a grad) for the staggered stencil; a_max = c0 + sum |amp|.
     """
     lam = stencil_symbol_max(cfg.stencil_order)
     omega = coef_upper_bound(cfg) * cfg.dim * lam / (dx * dx)
-    return cfg.dt_safety * heun_stability_limit(cfg.alpha_micro) / omega
+    return cfg.dt_safety * stability_limit(cfg.alpha_micro, getattr(cfg, "micro_stepper", 0)) / omega
 
 
 MACRO_DT_CONSTANT = 0.06
@@ -441,13 +456,16 @@ def _interior(arr: np.ndarray, d: int, r: int) -> Tuple:
 
 def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: float,
                 M: int, alpha_micro: float, W: np.ndarray, w: np.ndarray, order: int,
-                trace: bool = False):
+                trace: bool = False, stepper: int = 0):
     """One batch of micro problems with a common grid; returns H_avg (B, 3).
 
     m_init: (B, 3, N, ..., N). The micro problem (eq. micro) is stepped by HeunP
     (Section 3.1): k1 = f(m^n), k2 = f(m^n + dt k1) (reading G18: the standard
     Heun second stage, the one for which the stated update is second order),
-    m~ = m^n + dt/2 (k1 + k2), m^{n+1} = m~/|m~|. Only interior nodes move;
+    m~ = m^n + dt/2 (k1 + k2), m^{n+1} = m~/|m~|; with stepper = 1 by RK4P
+    (Section 3.1): k1 = f(m^n), k2 = f(m^n + dt/2 k1), k3 = f(m^n + dt/2 k2),
+    k4 = f(m^n + dt k3), m~ = m^n + dt/6 (k1 + 2 k2 + 2 k3 + k4), m^{n+1} =
+    m~/|m~| (reading G10 for the third stage). Only interior nodes move;
     ring nodes keep m_init (Dirichlet on m - m_init, Section 4.2).
     The average (eq. upscaling) is sum_n w_n sum_xi W(xi) H(m^n)(xi), with
     H(m^n) the stage-1 field of step n (reading G8); w_0 = w_M = 0.
@@ -473,10 +491,21 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
             break
         mi = m[inner]
         k1 = ll_rhs(mi, H1, alpha_micro, axis=cax)
-        ms = m.copy()
-        ms[inner] = mi + dt * k1
-        k2 = ll_rhs(ms[inner], field_H(ms, afaces, dx, order), alpha_micro, axis=cax)
-        mt = mi + 0.5 * dt * (k1 + k2)
+
+        def stage(c, k):
+            # f at the stage state m + c k (ring nodes keep m_init)
+            ms = m.copy()
+            ms[inner] = mi + c * k
+            return ll_rhs(ms[inner], field_H(ms, afaces, dx, order), alpha_micro, axis=cax)
+
+        if stepper == 0:
+            k2 = stage(dt, k1)
+            mt = mi + 0.5 * dt * (k1 + k2)
+        else:
+            k2 = stage(0.5 * dt, k1)
+            k3 = stage(0.5 * dt, k2)
+            k4 = stage(dt, k3)
+            mt = mi + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
         m[inner] = mt / np.sqrt((mt ** 2).sum(cax, keepdims=True))
     if trace:
         return S, m, np.array(energies), np.array(normdev)
@@ -518,7 +547,7 @@ def micro_batch(cfg, M: np.ndarray, points: Optional[Sequence[int]] = None,
             mi = np.stack([micro_initial(cfg, M, geos[i], dtype=dtype) for i in chunk])
             af = [np.stack([face_coefficients(cfg, geos[i], dtype)[k] for i in chunk]) for k in range(d)]
             S = micro_solve(mi, af, dtype(dx), dtype(dt), cfg.micro_steps, dtype(cfg.alpha_micro),
-                            W, w, cfg.stencil_order)
+                            W, w, cfg.stencil_order, stepper=getattr(cfg, "micro_stepper", 0))
             for j, i in enumerate(chunk):
                 out[:, i] = S[j]
     return out

@@ -39,7 +39,7 @@ class HmmParams(ctypes.Structure):
                 ("pts_per_eps", c_double), ("mu_over_eps", c_double), ("micro_steps", c_int),
                 ("dt_safety", c_double), ("px", c_int), ("qx", c_int), ("pt", c_int), ("qt", c_int),
                 ("interp_order", c_int), ("stencil_order", c_int), ("precision", c_int),
-                ("kernel_variant", c_int), ("reserved", c_int * 4)]
+                ("kernel_variant", c_int), ("micro_stepper", c_int), ("reserved", c_int * 3)]
 
 
 class HmmError(RuntimeError):
@@ -127,6 +127,7 @@ def make_params(cfg, precision=None, kernel_variant=0):
     p.stencil_order = int(cfg.stencil_order)
     p.precision = int(cfg.precision if precision is None else precision)
     p.kernel_variant = int(kernel_variant)
+    p.micro_stepper = int(getattr(cfg, "micro_stepper", 0))
     return p, keep
 
 

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <complex>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -201,11 +202,30 @@ double heun_limit(double a) {
   return lo;
 }
 
-double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order,
-                double dx) {
+double rk4_limit(double a) {
+  // scan outward from s = 0 for the first exit from the unit disc, then bisect
+  auto amp = [a](double s) {
+    const std::complex<double> z = s * std::complex<double>(-a, 1.0);
+    return std::abs(1.0 + z * (1.0 + z * (0.5 + z * (1.0 / 6.0 + z / 24.0))));
+  };
+  double lo = 0.0, hi = 1e-3;
+  while (amp(hi) <= 1.0) {
+    lo = hi;
+    hi += 1e-3;
+    if (hi > 20.0) return 0.0;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (amp(mid) <= 1.0) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order, double dx,
+                int stepper) {
   const double lam = stencil_order == 2 ? 4.0 : (28.0 / 12.0) * (28.0 / 12.0);
   const double omega = a_max * dim * lam / (dx * dx);
-  return dt_safety * heun_limit(alpha_micro) / omega;
+  return dt_safety * (stepper == 1 ? rk4_limit(alpha_micro) : heun_limit(alpha_micro)) / omega;
 }
 
 }  // namespace host
@@ -313,8 +333,10 @@ int max_n_for_dim(int d) { return d == 1 ? 1024 : (d == 2 ? 256 : 64); }
 hmm_status build(HmmHandle* h) {
   hmm_params& p = h->p;
   if (p.dim < 1 || p.dim > 3) return fail(h, HMM_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (p.reserved[i] != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
+    return fail(h, HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
   h->dim = p.dim;
   if (!(p.L > 0)) p.L = 1.0;
   if (p.px <= 0) p.px = 3;
@@ -412,7 +434,7 @@ hmm_status build(HmmHandle* h) {
     bd.dx = bd.eps / p.pts_per_eps;
     const double mup = (bd.N - 1) * bd.dx / 2.0;
     const double mu = p.mu_over_eps > 0 ? p.mu_over_eps * bd.eps : 0.8 * mup;
-    bd.dt = host::micro_dt(p.dt_safety, p.alpha_micro, h->a_max, h->dim, p.stencil_order, bd.dx);
+    bd.dt = host::micro_dt(p.dt_safety, p.alpha_micro, h->a_max, h->dim, p.stencil_order, bd.dx, p.micro_stepper);
     if (!(bd.dt > 0)) return fail(h, HMM_ERR_INVALID_ARG, "micro time step is not positive");
     auto it = class_ofs.find(bd.N);
     if (it == class_ofs.end()) {
@@ -496,8 +518,8 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  std::string why = "the resident kernels need the FP32 form and d = 2 or 3";
-  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 &&
+  std::string why = "the resident kernels need the FP32 form, HeunP and d = 2 or 3";
+  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 && p.micro_stepper == HMM_HEUNP &&
                       res2d_make_plan(h->dim, h->boxes.data(), h->P, h->radius, h->interp_k, p.n_terms,
                                       (size_t)optin - 256, &h->plan, &why) &&
                       (int)h->plan.groups.size() <= kQueues;
@@ -538,6 +560,7 @@ hmm_status build(HmmHandle* h) {
   }
   a.interp_k = h->interp_k;
   a.msteps = M;
+  a.stepper = p.micro_stepper;
   a.alpha_micro = p.alpha_micro;
   a.W64 = h->d_W64;
   a.W32 = h->d_W32;

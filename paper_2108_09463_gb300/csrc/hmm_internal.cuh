@@ -47,6 +47,7 @@ struct MicroArgs {
   double DX[3];
   int interp_k;          // k of Q_[2k]
   int msteps;            // M micro steps
+  int stepper;           // 0: HeunP, 1: RK4P (generic kernels)
   double alpha_micro;
   const double* W64;     // spatial weight tables (per size class)
   const float* W32;
@@ -123,8 +124,10 @@ bool kernel_coeffs(int p, int q, bool one_sided, double* out);   // out[p + 1]
 double eval_kernel(const double* c, int p, int q, double x);
 double eval_kernel0(const double* c, int p, int q, double t);
 double heun_limit(double alpha);
-double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order,
-                double dx);
+// Largest s with |1 + z + z^2/2 + z^3/6 + z^4/24| <= 1 on z = s(-alpha + i) (RK4P).
+double rk4_limit(double alpha);
+double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order, double dx,
+                int stepper);
 }  // namespace host
 
 }  // namespace hmm

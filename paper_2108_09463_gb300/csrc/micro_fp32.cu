@@ -33,16 +33,17 @@ struct Fp32Slot {
   float* vA;     // [3][cap] v_hi at step n
   float* vB;     // [3][cap] stage state v_hi + dt k1
   float* vlo;    // [3][cap] carried rounding error of v
-  float* k1;     // [3][cap] stage-1 slope
+  float* k1;     // [3][cap] stage-1 slope (RK4P: k1 + 2 k2 + 2 k3)
   float* V;      // [3][cap] sum_n w_n v_hi^n
   float* Vc;     // [3][cap] Kahan compensation of V
+  float* vC;     // [3][cap] second stage state (RK4P)
 };
 
 __host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 __host__ __device__ inline size_t fp32_slot_bytes(int D, size_t cap) {
   return align256(3 * cap * 8) + align256(D * cap * 8) + 2 * align256(3 * cap * 4) +
-         align256(D * cap * 4) + 6 * align256(3 * cap * 4);
+         align256(D * cap * 4) + 7 * align256(3 * cap * 4);
 }
 
 __device__ inline Fp32Slot carve_fp32(char* base, int D, size_t cap) {
@@ -60,6 +61,7 @@ __device__ inline Fp32Slot carve_fp32(char* base, int D, size_t cap) {
   s.k1 = reinterpret_cast<float*>(take(3 * cap * 4));
   s.V = reinterpret_cast<float*>(take(3 * cap * 4));
   s.Vc = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.vC = reinterpret_cast<float*>(take(3 * cap * 4));
   return s;
 }
 
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
         sl.mi32[o] = (float)mv;
         sl.vA[o] = 0.f;
         sl.vB[o] = 0.f;
+        sl.vC[o] = 0.f;
         sl.vlo[o] = 0.f;
         sl.V[o] = 0.f;
         sl.Vc[o] = 0.f;
@@ -178,6 +181,10 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
     __syncthreads();
 
     const float dt = (float)bd.dt, hdt = 0.5f * (float)bd.dt;
+    const bool rk4 = a.stepper == 1;
+    // HeunP: v_B = v + dt k1, d = dt/2 (k1 + k2). RK4P: v_B = v + dt/2 k1, the sum
+    // k1 + 2 k2 + 2 k3 accumulated in sl.k1, d = dt/6 (k1 + 2 k2 + 2 k3 + k4).
+    const float cb1 = rk4 ? hdt : dt, cdl = rk4 ? (float)(bd.dt / 6.0) : hdt;
     for (int n = 0; n < a.msteps; ++n) {
       const float wn = a.w32[n];
       // Stage 1: k1 = f(m_init + v), v_B = v + dt k1, V += w_n v (Kahan).
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
         for (int c = 0; c < 3; ++c) {
           const size_t o = c * cap + idx;
           sl.k1[o] = k1[c];
-          sl.vB[o] = v[c] + dt * k1[c];
+          sl.vB[o] = v[c] + cb1 * k1[c];
           const float y = wn * v[c] - sl.Vc[o];
           const float tV = sl.V[o] + y;
           sl.Vc[o] = (tV - sl.V[o]) - y;
@@ -206,8 +213,37 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
         }
       }
       __syncthreads();
-      // Stage 2: k2 = f(m_init + v_B); the step's increment d = dt/2 (k1 + k2) plus
-      // the projection, added to v = v_hi + v_lo with an exact error term.
+      if (rk4) {
+        // RK4P stages 2 and 3: k2 = f(m_init + v + dt/2 k1) (state in v_B), k3 =
+        // f(m_init + v + dt/2 k2) (state in v_C); the last stage's state v + dt k3 goes to v_B.
+        for (int stage = 2; stage <= 3; ++stage) {
+          const float* src = stage == 2 ? sl.vB : sl.vC;
+          float* dst = stage == 2 ? sl.vC : sl.vB;
+          const float cn = stage == 2 ? hdt : dt;
+          for (int t = tid; t < nint; t += nt) {
+            const int idx = interior_node<D, R>(t, N);
+            float Hv[3];
+            stencil_H<D, R, float>(src, sl.af32, cap, st, idx, cs, Hv);
+            float m[3], k[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              Hv[c] += sl.hi32[c * cap + idx];
+              m[c] = sl.mi32[c * cap + idx] + src[c * cap + idx];
+            }
+            ll_rhs(m, Hv, am, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const size_t o = c * cap + idx;
+              sl.k1[o] += 2.f * k[c];
+              dst[o] = sl.vA[o] + cn * k[c];
+            }
+          }
+          __syncthreads();
+        }
+      }
+      // Last stage: k = f(m_init + v_B); the step's increment d = cdl (sum of the
+      // earlier slopes + k) plus the projection, added to v = v_hi + v_lo with an
+      // exact error term.
       for (int t = tid; t < nint; t += nt) {
         const int idx = interior_node<D, R>(t, N);
         float Hv[3];
@@ -224,7 +260,7 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           vh[c] = sl.vA[c * cap + idx];
-          d[c] = hdt * (sl.k1[c * cap + idx] + k2[c]);
+          d[c] = cdl * (sl.k1[c * cap + idx] + k2[c]);
           vt[c] = vh[c] + d[c];
         }
         const float s = 2.f * (mi[0] * vt[0] + mi[1] * vt[1] + mi[2] * vt[2]) +

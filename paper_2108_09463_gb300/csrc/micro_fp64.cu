@@ -1,5 +1,5 @@
 // Plain FP64 micro-batch kernel: the micro problem (eq. micro) of every macro
-// point, stepped by HeunP (Section 3.1) with the Dirichlet ring (Section 4.2),
+// point, stepped by HeunP or RK4P (Section 3.1) with the Dirichlet ring (Section 4.2),
 // and reduced by the kernel-weighted average (Section 2.3, eq. upscaling), all
 // in FP64 arithmetic. One CTA per box, boxes pulled from an atomic queue.
 //
@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
   double* hi = mi + 3 * cap;  // H(m_init)
   double* vA = hi + 3 * cap;
   double* vB = vA + 3 * cap;
-  double* q = vB + 3 * cap;
-  double* af = q + 3 * cap;
+  double* q = vB + 3 * cap;   // the step's accumulated state v + dt sum b_i k_i
+  double* vC = q + 3 * cap;   // second stage state (RK4P)
+  double* af = vC + 3 * cap;
 
   for (;;) {
     const int b = next_box(a.queue, &s_box);
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
         mi[c * cap + idx] = P[c] * inv;
         vA[c * cap + idx] = 0.0;
         vB[c * cap + idx] = 0.0;
+        vC[c * cap + idx] = 0.0;
       }
       int j[3];
       node_coords<D>(idx, N, j);
@@ -66,6 +68,9 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
     __syncthreads();
 
     const double dt = bd.dt, hdt = 0.5 * bd.dt;
+    const bool rk4 = a.stepper == 1;
+    // stage-1 coefficients: q = v + cq1 k1, vB = v + cb1 k1; the last stage adds cql k_last
+    const double cq1 = rk4 ? dt / 6.0 : hdt, cb1 = rk4 ? hdt : dt, cql = rk4 ? dt / 6.0 : hdt;
     const double cs = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
     const double* W1 = a.W64 + bd.wofs;
     const int nint = ipow<D>(N - 2 * R);
@@ -127,13 +132,40 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
         ll_rhs(m, H, a.alpha_micro, k1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          q[c * cap + idx] = v[c] + hdt * k1[c];
-          vB[c * cap + idx] = v[c] + dt * k1[c];
+          q[c * cap + idx] = v[c] + cq1 * k1[c];
+          vB[c * cap + idx] = v[c] + cb1 * k1[c];
         }
       }
       if (n == a.msteps) break;
       __syncthreads();
-      // Stage 2: k2 = f(m + dt k1), m^{n+1} = normalise(m + dt/2 (k1 + k2)), as v.
+      if (rk4) {
+        // RK4P stages 2 and 3: k2 = f(v + dt/2 k1) (state in vB), k3 = f(v + dt/2 k2)
+        // (state in vC); q += dt/3 (k2 + k3); the last stage's state v + dt k3 goes to vB.
+        for (int stage = 2; stage <= 3; ++stage) {
+          const double* src = stage == 2 ? vB : vC;
+          double* dst = stage == 2 ? vC : vB;
+          const double cn = stage == 2 ? hdt : dt;
+          for (int t = tid; t < nint; t += nt) {
+            const int idx = interior_node<D, R>(t, N);
+            double Hv[3];
+            stencil_H<D, R, double>(src, af, cap, st, idx, cs, Hv);
+            double m[3], H[3], k[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              m[c] = mi[c * cap + idx] + src[c * cap + idx];
+              H[c] = hi[c * cap + idx] + Hv[c];
+            }
+            ll_rhs(m, H, a.alpha_micro, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              q[c * cap + idx] += (dt / 3.0) * k[c];
+              dst[c * cap + idx] = vA[c * cap + idx] + cn * k[c];
+            }
+          }
+          __syncthreads();
+        }
+      }
+      // Last stage: k = f(m_init + vB), m^{n+1} = normalise(m_init + q + cql k), as v.
       for (int t = tid; t < nint; t += nt) {
         const int idx = interior_node<D, R>(t, N);
         double Hv[3];
@@ -148,7 +180,7 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
         ll_rhs(m, H, a.alpha_micro, k2);
         double vt[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) vt[c] = q[c * cap + idx] + hdt * k2[c];
+        for (int c = 0; c < 3; ++c) vt[c] = q[c * cap + idx] + cql * k2[c];
         const double s = 2.0 * (mv[0] * vt[0] + mv[1] * vt[1] + mv[2] * vt[2]) +
                          (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) +
                          ((mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2]) - 1.0);
@@ -224,7 +256,7 @@ size_t micro_smem_bytes(int dim, int nmax, int interp_k, int n_terms) {
 size_t micro_slot_bytes_fp64(int dim, int nmax) {
   size_t cap = 1;
   for (int i = 0; i < dim; ++i) cap *= (size_t)nmax;
-  size_t b = (size_t)(5 * 3 + dim) * cap * sizeof(double);
+  size_t b = (size_t)(6 * 3 + dim) * cap * sizeof(double);
   return (b + 255) & ~(size_t)255;
 }
 

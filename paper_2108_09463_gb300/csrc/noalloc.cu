@@ -108,8 +108,10 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point runs the FP32 form only");
   if (p.eps_field || p.box_n_field)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point needs uniform eps and N");
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (p.reserved[i] != 0) return noalloc_fail(HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
+    return noalloc_fail(HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
   if (p.kernel_variant != 0 && p.kernel_variant != 1)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point runs the generic kernel");
   if (!(p.L > 0)) p.L = 1.0;
@@ -166,7 +168,7 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
   const double dx = p.eps / p.pts_per_eps;
   const double mup = (N - 1) * dx / 2.0;
   const double mu = p.mu_over_eps > 0 ? p.mu_over_eps * p.eps : 0.8 * mup;
-  const double dt = host::micro_dt(p.dt_safety, p.alpha_micro, a_max, p.dim, p.stencil_order, dx);
+  const double dt = host::micro_dt(p.dt_safety, p.alpha_micro, a_max, p.dim, p.stencil_order, dx, p.micro_stepper);
   if (!(dt > 0)) return noalloc_fail(HMM_ERR_INVALID_ARG, "micro time step is not positive");
   const int M = p.micro_steps;
 
@@ -251,6 +253,7 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
   }
   a.interp_k = k;
   a.msteps = M;
+  a.stepper = p.micro_stepper;
   a.alpha_micro = p.alpha_micro;
   a.W64 = reinterpret_cast<const double*>(base + o_W64);
   a.W32 = reinterpret_cast<const float*>(base + o_W32);

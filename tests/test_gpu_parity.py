@@ -96,6 +96,38 @@ def test_small_parity(torch_cuda, case, precision):
         assert abs(info["mu"][p] / geo["mu"] - 1) < 1e-14
 
 
+# The RK4P micro stepper (Section 3.1) on the generic kernels, both precisions.
+RK4P = {
+    "1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=60, micro_stepper=1)),
+    "2d": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=40, micro_stepper=1)),
+    "2d_low_damping": ("c5_sweep", dict(n_macro=(8, 8, 1), box_n=32, micro_steps=40, alpha_micro=0.01,
+                                        micro_stepper=1)),
+    "3d": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=16, mu_over_eps=0.9, micro_steps=20, micro_stepper=1)),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(RK4P))
+def test_rk4p_parity(torch_cuda, case, precision):
+    name, over = RK4P[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, precision)
+    pts, Hr = reference(cfg, M0, precision)
+    e = rel_err(Hg if pts is None else Hg[:, pts], Hr)
+    assert e < TOL[precision], (case, precision, e)
+    geo = O.box_geometry(cfg, 0)
+    assert abs(info["dt"][0] / geo["dt"] - 1) < 1e-12   # the RK4P stability limit, host vs oracle
+
+
+def test_rk4p_rejected_by_resident_kernels(torch_cuda):
+    from paper_2108_09463_gb300 import HMM, HmmError
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=10, micro_stepper=1)
+    with pytest.raises(HmmError) as ei:
+        HMM(cfg, precision=1, kernel_variant=2)
+    assert ei.value.status == 1
+
+
 def _uneven_small():
     cfg = W.config("c3_2d_uneven", n_macro=(12, 12, 1), micro_steps=40, eps_field=None, box_n_field=None)
     eps, n = W.uneven_eps_and_n(cfg, K=8.0, mu_prime=0.0075, nmin=24, nmax=48, step=8)

@@ -137,3 +137,49 @@ def test_ll_rhs_hand_value():
     """f(e_z, e_x) = -e_z x e_x - alpha e_z x (e_z x e_x) = (alpha, -1, 0)."""
     f = O.ll_rhs(np.array([0.0, 0.0, 1.0]), np.array([1.0, 0.0, 0.0]), 0.3)
     np.testing.assert_allclose(f, [0.3, -1.0, 0.0], atol=1e-15)
+
+
+def test_stepper_stability_limits_textbook_values():
+    """RK4's stability interval on the imaginary axis is 2 sqrt(2); on the negative
+    real axis both polynomials exit the unit disc at their textbook real limits
+    (2 for Heun, 2.785293563405... for RK4), approached here with alpha -> infinity."""
+    assert abs(O.stability_limit(1e-9, 1) - 2.0 * np.sqrt(2.0)) < 1e-6
+    a = 1e4
+    assert abs(O.stability_limit(a, 1) * abs(complex(-a, 1.0)) - 2.785293563405282) < 1e-4
+    assert abs(O.stability_limit(a, 0) * abs(complex(-a, 1.0)) - 2.0) < 1e-4
+    # HeunP's limit vanishes on the imaginary axis, RK4P's does not (Section 3.2)
+    assert O.stability_limit(1e-4, 0) < 0.1 and O.stability_limit(1e-4, 1) > 2.8
+
+
+def test_rk4p_fourth_order_in_time():
+    cfg = W.config("c1_1d", n_macro=(16, 1, 1), box_n=41, micro_steps=10)
+    M0 = W.initial_field(cfg)
+    geo, mi, af, Wd, _ = _one_box(cfg, 5, M0)
+    T = 40 * geo["dt"]
+
+    def final(nsteps, stepper=1):
+        w = np.zeros(nsteps + 1)
+        _, m, _, _ = O.micro_solve(mi, af, geo["dx"], T / nsteps, nsteps, cfg.alpha_micro, Wd, w, 4,
+                                   trace=True, stepper=stepper)
+        return m
+
+    ref = final(40 * 32)
+    errs = [np.abs(final(40 * s) - ref).max() for s in (1, 2, 4)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.6) and np.all(rates < 4.4), (errs, rates)
+    # HeunP and RK4P approximate the same solution
+    assert np.abs(final(40 * 8, stepper=0) - ref).max() < 1e-3 * np.abs(ref - mi).max()
+
+
+def test_rk4p_micro_batch_close_to_heunp():
+    """At the same micro time and a small step, the two steppers give the same average."""
+    cfg = W.config("c1_1d", n_macro=(16, 1, 1), box_n=81, micro_steps=240, dt_safety=0.2)
+    M0 = W.initial_field(cfg)
+    H0 = O.micro_batch(cfg, M0, points=[3, 9])
+    dt0 = O.micro_dt(cfg, cfg.eps / cfg.pts_per_eps)
+    cfg1 = cfg.replace(micro_stepper=1)
+    dt1 = O.micro_dt(cfg1, cfg.eps / cfg.pts_per_eps)
+    cfg1 = cfg1.replace(micro_steps=int(round(240 * dt0 / dt1)))
+    cfg1 = cfg1.replace(dt_safety=cfg.dt_safety * dt0 * 240 / (cfg1.micro_steps * dt1))
+    H1 = O.micro_batch(cfg1, M0, points=[3, 9])
+    assert np.abs(H1 - H0).max() < 1e-3 * np.abs(H0).max(), (H0, H1)

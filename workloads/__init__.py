@@ -59,11 +59,12 @@ class HMMConfig:
     pts_per_eps              K: micro grid spacing dx = eps/K
     mu_over_eps              averaging half-width mu/eps (<= 0: mu = 0.8*mu')
     micro_steps              M: micro time steps per micro problem (eta = M*dt)
-    dt_safety                micro dt as a fraction of the HeunP stability limit
+    dt_safety                micro dt as a fraction of the stepper's stability limit
     px, qx, pt, qt           kernel parameters of K in K^{px,qx}, K0 in K0^{pt,qt}
     interp_order             2k of the normalised interpolation Q_[2k]
     stencil_order            2 or 4
     precision                0: plain FP64 method, 1: batched FP32 form
+    micro_stepper            0: HeunP, 1: RK4P (Section 3.1) for the micro problems
     """
     dim: int
     n_macro: Sequence[int]
@@ -88,6 +89,7 @@ class HMMConfig:
     interp_order: int = 4
     stencil_order: int = 4
     precision: int = 0
+    micro_stepper: int = 0
     name: str = ""
 
     @property
