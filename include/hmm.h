@@ -162,6 +162,21 @@ hmm_status hmm_stats(void* handle, double* lattice_updates_per_batch, double* la
  * macro-point order: dt_micro, mu, dx and N. Any pointer may be NULL. */
 hmm_status hmm_box_info(void* handle, double* dt, double* mu, double* dx, int* n);
 
+/* Replaces the coefficient of hmm_params (c0 and terms) by tabulated values of
+ * a^eps at every staggered face of every micro box, for coefficients that are
+ * not sums of separable terms (for example the locally periodic 2D coefficient
+ * of Section 5, eq. coeff_loc2D). table_host: FP64 host array, copied. The boxes
+ * follow one another in macro-point order; box p holds d blocks of N_p^d values,
+ * block k for the faces along axis k: entry idx (the C-order multi-index j of a
+ * box node, last axis fastest) is a^eps at x_p + xi_j + (dx/2) e_k, the face
+ * between node j and its +1 neighbour along axis k, with xi_j as in hmm_init
+ * (entries with j_k = N_p - 1 are not used). n_values: the array length, which
+ * must equal sum_p d N_p^d. Every used value must be positive and finite (A1).
+ * The micro time step of each box is recomputed from the maximum of its values,
+ * and the macro time step from the global maximum when dt_macro <= 0. A macro
+ * step graph captured earlier is discarded. Synchronises the handle's stream. */
+hmm_status hmm_set_face_table(void* handle, const double* table_host, long long n_values);
+
 /* The macro time step the handle uses. */
 hmm_status hmm_macro_dt(void* handle, double* dt_macro);
 

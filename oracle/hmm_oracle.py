@@ -209,7 +209,7 @@ def coef_upper_bound(cfg) -> float:
     return cfg.c0 + sum(abs(t.amp) for t in cfg.terms)
 
 
-def micro_dt(cfg, dx: float) -> float:
+def micro_dt(cfg, dx: float, a_max: Optional[float] = None) -> float:
     """Micro time step dt = safety * s_max(alpha_micro) / omega_max (reading G4), s_max
     the stability limit of the micro stepper (HeunP or RK4P).
 
@@ -217,7 +217,9 @@ def micro_dt(cfg, dx: float) -> float:
     -div(a grad) for the staggered stencil; a_max = c0 + sum |amp|.
     """
     lam = stencil_symbol_max(cfg.stencil_order)
-    omega = coef_upper_bound(cfg) * cfg.dim * lam / (dx * dx)
+    if a_max is None:
+        a_max = coef_upper_bound(cfg)
+    omega = a_max * cfg.dim * lam / (dx * dx)
     return cfg.dt_safety * stability_limit(cfg.alpha_micro, getattr(cfg, "micro_stepper", 0)) / omega
 
 
@@ -229,7 +231,13 @@ def macro_dt(cfg) -> float:
     if cfg.dt_macro > 0:
         return cfg.dt_macro
     DX = min(cfg.L / n for n in list(cfg.n_macro)[: cfg.dim])
-    return MACRO_DT_CONSTANT * DX * DX / (cfg.dim * coef_upper_bound(cfg))
+    a_max = coef_upper_bound(cfg)
+    if getattr(cfg, "coef_fn", None) is not None:
+        a_max = 0.0
+        for p in range(cfg.n_points):
+            geo = box_geometry(cfg, p)
+            a_max = max(a_max, float(max(f.max() for f in face_coefficients(cfg, geo))))
+    return MACRO_DT_CONSTANT * DX * DX / (cfg.dim * a_max)
 
 
 # --------------------------------------------------------------------------
@@ -249,9 +257,16 @@ def box_geometry(cfg, p: int) -> Dict:
     mup = (N - 1) * dx / 2.0
     mu = cfg.mu_over_eps * eps if cfg.mu_over_eps > 0 else 0.8 * mup
     r = 1 if cfg.stencil_order == 2 else 3
-    return dict(p=int(p), idx=tuple(int(i) for i in idx), DX=DX,
-                xc=[idx[k] * DX[k] for k in range(d)], eps=eps, N=N, dx=dx,
-                mu_prime=mup, mu=mu, r=r, dt=micro_dt(cfg, dx), M=int(cfg.micro_steps))
+    geo = dict(p=int(p), idx=tuple(int(i) for i in idx), DX=DX,
+               xc=[idx[k] * DX[k] for k in range(d)], eps=eps, N=N, dx=dx,
+               mu_prime=mup, mu=mu, r=r, M=int(cfg.micro_steps))
+    # a_max: the bound c0 + sum |amp| of the separable terms, or, for a coefficient
+    # function, the maximum over this box's faces
+    a_max = None
+    if getattr(cfg, "coef_fn", None) is not None:
+        a_max = float(max(f.max() for f in face_coefficients(cfg, geo)))
+    geo["dt"] = micro_dt(cfg, dx, a_max)
+    return geo
 
 
 def node_offsets(N: int, dx: float, dtype=np.float64) -> np.ndarray:
@@ -319,7 +334,10 @@ def micro_initial(cfg, M: np.ndarray, geo: Dict, normalise: bool = True, dtype=n
 
 
 def coef_eval(cfg, eps: float, X: Sequence[np.ndarray], dtype=np.float64) -> np.ndarray:
-    """a(x) = c0 + sum_t amp_t prod_k g_tk(2 pi omega_tk s_k + phase_tk), s = x/eps or x."""
+    """a(x) = c0 + sum_t amp_t prod_k g_tk(2 pi omega_tk s_k + phase_tk), s = x/eps or x;
+    or the configuration's own coefficient function (cfg.coef_fn) when it has one."""
+    if getattr(cfg, "coef_fn", None) is not None:
+        return np.broadcast_to(np.asarray(cfg.coef_fn(list(X), eps), dtype=dtype), np.broadcast(*X).shape)
     out = np.full(np.broadcast(*X).shape, dtype(cfg.c0), dtype=dtype)
     two_pi = 2 * _pi(dtype)
     for t in cfg.terms:

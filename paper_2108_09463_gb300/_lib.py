@@ -22,8 +22,8 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 # The symbols include/hmm.h declares (checked by the CPU test suite).
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
             "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
-            "hmm_box_info", "hmm_macro_dt", "hmm_micro_batch_noalloc", "hmm_last_error",
-            "hmm_destroy")
+            "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
+            "hmm_last_error", "hmm_destroy")
 
 
 class HmmCoefTerm(ctypes.Structure):
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_stats.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
     lib.hmm_box_info.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.hmm_macro_dt.argtypes = [c_void_p, POINTER(c_double)]
+    lib.hmm_set_face_table.argtypes = [c_void_p, c_void_p, ctypes.c_longlong]
     lib.hmm_micro_batch_noalloc.argtypes = [POINTER(HmmParams), c_void_p, c_void_p, c_void_p]
     lib.hmm_last_error.argtypes = [c_void_p]
     lib.hmm_last_error.restype = c_char_p
@@ -138,7 +139,7 @@ def _ptr(t) -> int:
 class HMM:
     """One HMM problem on the current CUDA device (a handle of the C ABI)."""
 
-    def __init__(self, cfg, precision=None, stream=None, kernel_variant=0):
+    def __init__(self, cfg, precision=None, stream=None, kernel_variant=0, face_table=None):
         import torch
         self.lib = load_library()
         self.cfg = cfg
@@ -153,6 +154,14 @@ class HMM:
         if st != HMM_OK:
             raise HmmError(st, self.lib.hmm_last_error(None).decode())
         self.h = h
+        if face_table is not None:
+            self.set_face_table(face_table)
+
+    def set_face_table(self, table):
+        """Tabulated a^eps at every face of every box (see hmm_set_face_table)."""
+        import numpy as np
+        t = np.ascontiguousarray(table, dtype=np.float64)
+        self._check(self.lib.hmm_set_face_table(self.h, t.ctypes.data, int(t.size)))
 
     def _check(self, st):
         if st != HMM_OK:

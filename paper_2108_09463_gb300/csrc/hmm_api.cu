@@ -278,6 +278,8 @@ struct HmmHandle {
   bool res2d = false;        // resident 2D FP32 kernel
   Res2dPlan plan;            // its work items and launches
   int2* d_items = nullptr;
+  double* d_faces = nullptr;      // tabulated face coefficients (hmm_set_face_table)
+  long long* d_face_off = nullptr;
   int* d_queue = nullptr;
   int* d_err = nullptr;
   int* h_err = nullptr;      // pinned
@@ -316,7 +318,7 @@ hmm_status cuda_fail(HmmHandle* h, cudaError_t e, const char* where) {
 
 void free_all(HmmHandle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue, h->d_items,
+  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue, h->d_items, h->d_faces, h->d_face_off,
                   h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -814,6 +816,78 @@ hmm_status hmm_box_info(void* handle, double* dt, double* mu, double* dx, int* n
   if (mu) std::memcpy(mu, h->box_mu.data(), sizeof(double) * h->P);
   if (dx) std::memcpy(dx, h->box_dx.data(), sizeof(double) * h->P);
   if (n) std::memcpy(n, h->box_n.data(), sizeof(int) * h->P);
+  return HMM_OK;
+}
+
+hmm_status hmm_set_face_table(void* handle, const double* table_host, long long n_values) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!table_host) return fail(h, HMM_ERR_INVALID_ARG, "null face table");
+  const int d = h->dim;
+  std::vector<long long> off(h->P);
+  long long total = 0;
+  for (int q = 0; q < h->P; ++q) {
+    long long nd = 1;
+    for (int k = 0; k < d; ++k) nd *= h->box_n[q];
+    off[q] = total;
+    total += d * nd;
+  }
+  if (n_values != total) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "face table has %lld values, the boxes need %lld", n_values, total);
+    return fail(h, HMM_ERR_INVALID_ARG, msg);
+  }
+  // each box's maximum over the faces the stencil uses (node index j_k < N - 1); (A1)
+  std::vector<double> bmax(h->P, 0.0);
+  double gmax = 0.0;
+  for (int q = 0; q < h->P; ++q) {
+    const int N = h->box_n[q];
+    long long nd = 1;
+    for (int k = 0; k < d; ++k) nd *= N;
+    for (int k = 0; k < d; ++k) {
+      long long stride = 1;
+      for (int a = k + 1; a < d; ++a) stride *= N;
+      const double* blk = table_host + off[q] + k * nd;
+      for (long long idx = 0; idx < nd; ++idx) {
+        if ((idx / stride) % N == N - 1) continue;
+        const double v = blk[idx];
+        if (!(v > 0.0) || !std::isfinite(v))
+          return fail(h, HMM_ERR_INVALID_ARG, "face table: a^eps must be positive and finite at every used face (A1)");
+        bmax[q] = std::max(bmax[q], v);
+      }
+    }
+    gmax = std::max(gmax, bmax[q]);
+  }
+  HMM_CUDA(h, cudaStreamSynchronize(h->stream));   // no batch in flight reads the old table
+  if (h->d_faces) cudaFree(h->d_faces);
+  if (h->d_face_off) cudaFree(h->d_face_off);
+  h->d_faces = nullptr;
+  h->d_face_off = nullptr;
+  HMM_CUDA(h, cudaMalloc(&h->d_faces, sizeof(double) * (size_t)total));
+  HMM_CUDA(h, cudaMalloc(&h->d_face_off, sizeof(long long) * (size_t)h->P));
+  HMM_CUDA(h, cudaMemcpy(h->d_faces, table_host, sizeof(double) * (size_t)total, cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_face_off, off.data(), sizeof(long long) * (size_t)h->P, cudaMemcpyHostToDevice));
+  // micro time steps from each box's maximum; the macro step from the global one when
+  // the library chose it
+  const hmm_params& p = h->p;
+  for (BoxDesc& bd : h->boxes) {
+    bd.dt = host::micro_dt(p.dt_safety, p.alpha_micro, bmax[bd.p], d, p.stencil_order, bd.dx, p.micro_stepper);
+    h->box_dt[bd.p] = bd.dt;
+  }
+  HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->P, cudaMemcpyHostToDevice));
+  h->a_max = gmax;
+  if (!(p.dt_macro > 0)) {
+    double dX = h->DX[0];
+    for (int k = 1; k < d; ++k) dX = std::min(dX, h->DX[k]);
+    h->dt_macro = kMacroDtConstant * dX * dX / (d * gmax);
+  }
+  h->args.faces = h->d_faces;
+  h->args.face_off = h->d_face_off;
+  if (h->graph) {   // captured with the old arguments
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_M = nullptr;
+  }
   return HMM_OK;
 }
 

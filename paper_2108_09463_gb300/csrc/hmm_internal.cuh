@@ -48,6 +48,8 @@ struct MicroArgs {
   int interp_k;          // k of Q_[2k]
   int msteps;            // M micro steps
   int stepper;           // 0: HeunP, 1: RK4P (generic kernels)
+  const double* faces;   // tabulated a^eps at the faces (NULL: c0 + terms), see hmm_set_face_table
+  const long long* face_off;   // offset of macro point p's block in faces
   double alpha_micro;
   const double* W64;     // spatial weight tables (per size class)
   const float* W32;

@@ -248,4 +248,14 @@ __device__ __forceinline__ double face_coef(const MicroArgs& a, const SetupSmem&
   return out;
 }
 
+// a^eps at the face between node idx of box bd and its +1 neighbour along axis k:
+// from the caller's table when one is set (macro point bd.p's block, d sub-blocks of
+// N^d values), else from the separable terms.
+template <int D>
+__device__ __forceinline__ double face_value(const MicroArgs& a, const BoxDesc& bd, const SetupSmem& sm, int N,
+                                             int idx, int k) {
+  if (a.faces) return a.faces[a.face_off[bd.p] + (long long)k * ipow<D>(N) + idx];
+  return face_coef<D>(a, sm, N, idx, k);
+}
+
 }  // namespace hmm

@@ -406,7 +406,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         for (int k = 0; k < D; ++k) {
           double v = 0.0;
           if (j[k] < N - 1) {
-            v = face_coef<D>(a, smr, N, idx, k);
+            v = face_value<D>(a, bd, smr, N, idx, k);
             bad |= !(v > 0.0);
           }
           af64[k * cap + idx] = v;

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
       for (int k = 0; k < D; ++k) {
         double v = 0.0;
         if (j[k] < N - 1) {
-          v = face_coef<D>(a, sm, N, idx, k);
+          v = face_value<D>(a, bd, sm, N, idx, k);
           bad |= !(v > 0.0);
         }
         af[k * cap + idx] = v;

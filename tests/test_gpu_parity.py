@@ -128,6 +128,49 @@ def test_rk4p_rejected_by_resident_kernels(torch_cuda):
     assert ei.value.status == 1
 
 
+# Coefficients that are not sums of separable terms, tabulated at the faces
+# (hmm_set_face_table): the locally periodic 2D example of Section 5 and a 1D one.
+TABLE = {
+    "loc2d": ("ex_loc2d", dict(n_macro=(6, 5, 1), box_n=29, mu_over_eps=0.0, micro_steps=40)),
+    "loc1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=60,
+                            coef_fn=lambda X, eps: 1.1 + 0.25 * np.sin(2 * np.pi * X[0] + 1.1)
+                            + 0.5 * np.sin(2 * np.pi * X[0] / eps))),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(TABLE))
+def test_face_table_parity(torch_cuda, case, precision):
+    from paper_2108_09463_gb300 import HMM
+    name, over = TABLE[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    h = HMM(cfg, precision=precision, face_table=W.face_table(cfg))
+    Hg = h.micro_batch(torch_cuda.from_numpy(M0).cuda()).cpu().numpy()
+    info = h.box_info()
+    assert abs(h.macro_dt() / O.macro_dt(cfg) - 1) < 1e-12
+    h.close()
+    for p in (0, cfg.n_points - 1):   # the micro step from each box's own maximum
+        assert abs(info["dt"][p] / O.box_geometry(cfg, p)["dt"] - 1) < 1e-12
+    pts, Hr = reference(cfg, M0, precision)
+    e = rel_err(Hg if pts is None else Hg[:, pts], Hr)
+    assert e < TOL[precision], (case, precision, e)
+
+
+def test_face_table_rejects_bad_tables(torch_cuda):
+    from paper_2108_09463_gb300 import HMM, HmmError
+    cfg = W.config("ex_loc2d", n_macro=(6, 5, 1), box_n=29, mu_over_eps=0.0, micro_steps=10)
+    tab = W.face_table(cfg)
+    h = HMM(cfg, precision=1)
+    with pytest.raises(HmmError):
+        h.set_face_table(tab[:-1])          # wrong length
+    bad = tab.copy()
+    bad[5] = -1.0                           # a used face of box 0, axis 0: (A1)
+    with pytest.raises(HmmError):
+        h.set_face_table(bad)
+    h.close()
+
+
 def _uneven_small():
     cfg = W.config("c3_2d_uneven", n_macro=(12, 12, 1), micro_steps=40, eps_field=None, box_n_field=None)
     eps, n = W.uneven_eps_and_n(cfg, K=8.0, mu_prime=0.0075, nmin=24, nmax=48, step=8)

@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional, Sequence
+from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
@@ -65,6 +65,9 @@ class HMMConfig:
     stencil_order            2 or 4
     precision                0: plain FP64 method, 1: batched FP32 form
     micro_stepper            0: HeunP, 1: RK4P (Section 3.1) for the micro problems
+    coef_fn                  a coefficient that is not a sum of separable terms:
+                             coef_fn(X, eps) -> a at the points X (a list of d
+                             coordinate arrays); replaces c0 + terms when set
     """
     dim: int
     n_macro: Sequence[int]
@@ -90,6 +93,7 @@ class HMMConfig:
     stencil_order: int = 4
     precision: int = 0
     micro_stepper: int = 0
+    coef_fn: Optional[Callable] = None
     name: str = ""
 
     @property
@@ -189,6 +193,43 @@ def c1_initial(x: np.ndarray) -> np.ndarray:
     return mt / np.sqrt((mt ** 2).sum(0))
 
 
+def coeff_loc2d(X, eps):
+    """The locally periodic 2D coefficient of Section 5 (eq. coeff_loc2D):
+    0.25 exp(-cos(2 pi (x1 + x2)/eps) + sin(2 pi x1/eps) cos(2 pi x2))."""
+    x1, x2 = X[0], X[1]
+    tp = 2 * np.pi
+    return 0.25 * np.exp(-np.cos(tp * (x1 + x2) / eps) + np.sin(tp * x1 / eps) * np.cos(tp * x2))
+
+
+def face_table(cfg: HMMConfig) -> np.ndarray:
+    """cfg.coef_fn tabulated at every face of every micro box, in the layout of
+    hmm_set_face_table: boxes in macro-point order, per box d blocks of N^d values,
+    block k at x_p + xi_j + (dx/2) e_k with xi_j = (j - (N-1)/2) dx, dx = eps_p/K
+    (entries with j_k = N - 1 unused, set to 1)."""
+    d = cfg.dim
+    n = [int(v) for v in list(cfg.n_macro)[:d]]
+    DX = [cfg.L / nk for nk in n]
+    out = []
+    for p in range(cfg.n_points):
+        idx = np.unravel_index(p, n)
+        eps = float(cfg.eps_field[p]) if cfg.eps_field is not None else float(cfg.eps)
+        N = int(cfg.box_n_field[p]) if cfg.box_n_field is not None else int(cfg.box_n)
+        dx = eps / cfg.pts_per_eps
+        xi = (np.arange(N) - (N - 1) / 2.0) * dx
+        for k in range(d):
+            X = []
+            for a in range(d):
+                shp = [1] * d
+                shp[a] = N
+                X.append(idx[a] * DX[a] + (xi + (0.5 * dx if a == k else 0.0)).reshape(shp))
+            vals = np.broadcast_to(np.asarray(cfg.coef_fn(X, eps), dtype=np.float64), (N,) * d).copy()
+            last = [slice(None)] * d
+            last[k] = N - 1
+            vals[tuple(last)] = 1.0
+            out.append(vals.ravel())
+    return np.concatenate(out)
+
+
 def uneven_eps_and_n(cfg: HMMConfig, K: float = 8.0, mu_prime: float = 0.015,
                      nmin: int = 32, nmax: int = 96, step: int = 8):
     """Locally varying eps and box sizes for the uneven-box workload.
@@ -267,6 +308,13 @@ def config(name: str, **over) -> HMMConfig:
         cfg = HMMConfig(dim=2, n_macro=(32, 32, 1), alpha=0.1, alpha_micro=1.0,
                         c0=1.0, terms=[_term(0.9, _sin(0))], eps=1.0 / 400,
                         box_n=64, pts_per_eps=10.0, micro_steps=400, name=name)
+    elif name == "ex_loc2d":
+        # Section 5, locally periodic 2D example: eq. coeff_loc2D, alpha = 0.1,
+        # alpha_micro = 1.2, mu = 5 eps, mu' = 7 eps, eps = 0.01, (EX2) initial data,
+        # DX = 1/16; K = 8 points per eps (not stated) gives N = 2 mu' K + 1 = 113.
+        cfg = HMMConfig(dim=2, n_macro=(16, 16, 1), alpha=0.1, alpha_micro=1.2,
+                        c0=1.0, terms=[], eps=0.01, box_n=113, pts_per_eps=8.0,
+                        mu_over_eps=5.0, micro_steps=1250, coef_fn=coeff_loc2d, name=name)
     else:
         raise KeyError(name)
     cfg = dataclasses.replace(cfg, **over)
@@ -281,6 +329,8 @@ def initial_field(cfg: HMMConfig, seed: Optional[int] = None) -> np.ndarray:
     if cfg.dim == 1:
         x = macro_coords(cfg)[0]
         m = c1_initial(x)
+    elif cfg.name == "ex_loc2d":
+        m = ex2_initial(*_grid(cfg))
     else:
         base = 20210820
         s = base + (CONFIG_NAMES.index(cfg.name) if cfg.name in CONFIG_NAMES else 7)
