@@ -325,13 +325,16 @@ def run_micro_only(args, local_rank):
         over["box_n"] = args.box_n
     if args.alpha_micro:
         over["alpha_micro"] = args.alpha_micro
+    if args.micro_stepper:
+        over["micro_stepper"] = args.micro_stepper
     cfg = W.config(args.workload, **over)
     if args.workload == "c3_2d_uneven" and args.macro_grid:
         cfg = cfg.replace(eps_field=None, box_n_field=None)
         eps, nf = W.uneven_eps_and_n(cfg)
         cfg = cfg.replace(eps_field=eps, box_n_field=nf)
     prec = 0 if args.precision == "fp64" else 1
-    h = HMM(cfg, precision=prec, kernel_variant=args.variant)
+    table = W.face_table(cfg) if cfg.coef_fn is not None else None
+    h = HMM(cfg, precision=prec, kernel_variant=args.variant, face_table=table)
     M = torch.from_numpy(W.initial_field(cfg)).cuda()
     H = torch.empty_like(M)
     for _ in range(args.warmup):
@@ -343,7 +346,9 @@ def run_micro_only(args, local_rank):
     lu = h.stats()[0]
     rec = {"mode": "micro-only", "workload": args.workload, "boxes": cfg.n_points,
            "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
-           "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3), "ms": ms}
+           "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3), "ms": ms,
+           "micro_stepper": ["HeunP", "RK4P"][cfg.micro_stepper],
+           "micro_dt_mean": float(h.box_info()["dt"].mean()), "micro_steps": cfg.micro_steps}
     if args.cpu_baseline_micro:
         # the oracle on a spread sample of the same boxes, spawned processes on the host cores
         import multiprocessing as mp
@@ -419,7 +424,8 @@ def main():
     ap.add_argument("--box-n", type=int, default=None)
     ap.add_argument("--alpha-micro", type=float, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--variant", type=int, default=0, help="FP32 kernel: 0/1 generic, 2 resident 2D")
+    ap.add_argument("--variant", type=int, default=0, help="FP32 kernel: 0 automatic, 1 generic, 2 resident")
+    ap.add_argument("--micro-stepper", type=int, default=0, help="with --micro-only: 0 HeunP, 1 RK4P")
     ap.add_argument("--cpu-baseline-micro", action="store_true",
                     help="with --micro-only: also time the oracle on a sample of the boxes")
     ap.add_argument("--macro-steps", type=int, default=0,
