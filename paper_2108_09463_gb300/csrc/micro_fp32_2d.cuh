@@ -154,7 +154,8 @@ __host__ __device__ inline bool res_setup_fits(const ResDims& d, int N, int inte
   return setup_smem_doubles(2, N, interp_k, n_terms) * 2 <= (size_t)3 * d.rows * d.LD;
 }
 
-__host__ __device__ inline size_t res2d_arena_doubles(int nmax) { return (size_t)5 * nmax * nmax; }
+// per CTA: m_init (3), face coefficients (2), x- and y-face fluxes of m_init and W (4 + 4)
+__host__ __device__ inline size_t res2d_arena_doubles(int nmax) { return (size_t)13 * nmax * nmax; }
 
 
 // One persistent launch: its work items, its queue counter and its cluster size.
@@ -439,42 +440,53 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       }
       const double cs64 = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
       const double* W1d = a.W64 + bd.wofs;
+      // H(m_init) and H(W) in FP64, face fluxes first (each face once): components 0-2
+      // of m_init and, as a fourth, the weight W = W(x) W(y), whose face differences
+      // factor into 1D differences of the weight table. x-faces (between rows f and
+      // f+1, f in [xf0, xf1)) at the interior columns; y-faces (between columns g and
+      // g+1, g in [yg0, yg1)) at the slab's rows.
+      double* flx = af64 + 2 * cap;   // [4][cap] x-face fluxes at (f, j)
+      double* fly = flx + 4 * cap;    // [4][cap] y-face fluxes at (i, g)
+      const int fl = R == 3 ? 2 : 1, fh = R == 3 ? 1 : 0;   // a node uses faces i-fl .. i+fh
+      const int xf0 = r0 + R - fl, xf1 = r0 + S + R + fh, nxf = xf1 - xf0;
+      const int yg0 = R - fl, yg1 = N - R + fh, nyg = yg1 - yg0;
+      auto fdiff = [](const double* u, int o, int st_) {   // the face difference at face o
+        return R == 3 ? (u[o - st_] - u[o + 2 * st_]) + 27.0 * (u[o + st_] - u[o]) : u[o + st_] - u[o];
+      };
+      for (int e = tid; e < nxf * Ni; e += nt) {
+        const int f = xf0 + e / Ni, j = R + e % Ni;
+        const int o = f * N + j;
+        const double af = af64[o];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) flx[c * cap + o] = af * fdiff(mi64 + c * cap, o, N);
+        flx[3 * cap + o] = af * W1d[j] * fdiff(W1d, f, 1);
+      }
+      for (int e = tid; e < S * nyg; e += nt) {
+        const int i = r0 + R + e / nyg, g = yg0 + e % nyg;
+        const int o = i * N + g;
+        const double af = af64[cap + o];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fly[c * cap + o] = af * fdiff(mi64 + c * cap, o, 1);
+        fly[3 * cap + o] = af * W1d[i] * fdiff(W1d, g, 1);
+      }
+      __syncthreads();
+      auto fcomb = [](const double* F, int o, int st_) {   // node combination of the fluxes
+        return R == 3 ? (F[o - 2 * st_] - F[o + st_]) + 27.0 * (F[o] - F[o - st_]) : F[o] - F[o - st_];
+      };
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
       for (int e = tid; e < S * Ni; e += nt) {
         const int ii = e / Ni, jj = e - ii * Ni;
         const int idx = (r0 + ii + R) * N + (jj + R);
-        double H[3];
-        stencil_H<D, R, double>(mi64, af64, cap, st, idx, cs64, H);
+        double H[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) H[c] = (fcomb(flx + c * cap, idx, N) + fcomb(fly + c * cap, idx, 1)) * cs64;
         const double W = W1d[r0 + ii + R] * W1d[jj + R];
         s0 += W * H[0];
         s1 += W * H[1];
         s2 += W * H[2];
 #pragma unroll
         for (int c = 0; c < 3; ++c) hiS[(c * d.S + ii) * d.LDI + jj] = (float)H[c];
-        // H(W) with the same operator (W vanishes on and near the ring)
-        double hwd = 0.0;
-#pragma unroll 1
-        for (int k = 0; k < D; ++k) {
-          const int s = st.s[k];
-          const double* af = af64 + k * cap;
-          double Wv[7];
-#pragma unroll
-          for (int o = -R; o <= R; ++o) {
-            const int id = idx + o * s;
-            const int r_ = id / N, c_ = id - r_ * N;
-            Wv[o + R] = W1d[r_] * W1d[c_];
-          }
-          if (R == 1) {
-            hwd += af[idx] * (Wv[2] - Wv[1]) - af[idx - s] * (Wv[1] - Wv[0]);
-          } else {
-            const double g_2 = (Wv[0] - Wv[3]) + 27.0 * (Wv[2] - Wv[1]);
-            const double g_1 = (Wv[1] - Wv[4]) + 27.0 * (Wv[3] - Wv[2]);
-            const double g0 = (Wv[2] - Wv[5]) + 27.0 * (Wv[4] - Wv[3]);
-            const double g1 = (Wv[3] - Wv[6]) + 27.0 * (Wv[5] - Wv[4]);
-            hwd += (af[idx - 2 * s] * g_2 - af[idx + s] * g1) + 27.0 * (af[idx] * g0 - af[idx - s] * g_1);
-          }
-        }
-        hwS[ii * d.LDI + jj] = (float)(hwd * cs64);
+        hwS[ii * d.LDI + jj] = (float)H[3];
       }
       block_sum3(s0, s1, s2, red);
       if (tid == 0) {

@@ -86,7 +86,8 @@ __host__ __device__ inline int res3_r0(int q, int Ni, int cs) { return (q * Ni) 
 // The rank whose slab holds interior plane z.
 __host__ __device__ inline int res3_owner(int z, int Ni, int cs) { return ((z + 1) * cs - 1) / Ni; }
 
-__host__ __device__ inline size_t res3d_arena_doubles(int nmax) { return (size_t)6 * nmax * nmax * nmax; }
+// per CTA: m_init (3), face coefficients (3), face fluxes of m_init and W per axis (3 x 4)
+__host__ __device__ inline size_t res3d_arena_doubles(int nmax) { return (size_t)18 * nmax * nmax * nmax; }
 
 // y direction of the stencil for one plane and one component: rows y-r..y+r of the
 // plane (P points at the tile's row, column j0), faces between rows from fyp (the
@@ -324,15 +325,64 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         const int f = e / nn, yx = e - f * nn, y = yx / Ni, x = yx - y * Ni;
         fzS[f * d.PI + y * d.LDI + x] = (float)af64[bidx(r0 + f + f0, y + R, x + R)];
       }
-      const Strides<D> st(N);
       const double cs64 = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
       const double* W1d = a.W64 + bd.wofs;
+      // H(m_init) and H(W) in FP64, face fluxes first (each face once): components 0-2
+      // of m_init and, as a fourth, W = W(z) W(y) W(x), whose face differences factor
+      // into 1D differences of the weight table. Per axis k the fluxes at the faces
+      // between nodes j and j + e_k that the slab's interior nodes use.
+      double* fl3 = af64 + 3 * cap;   // [axis][4][cap]
+      const int fl = R == 3 ? 2 : 1, fh = R == 3 ? 1 : 0;   // a node uses faces j-fl .. j+fh
+      const int zf0 = r0 + R - fl, nzf = S + fl + fh;       // z-face planes
+      const int g0 = R - fl, ng = Ni + fl + fh;              // y- and x-face rows/columns
+      const int zo = r0 + R;                                 // first own plane (box coordinates)
+      auto fdiff = [](const double* u, size_t o, size_t st_) {
+        return R == 3 ? (u[o - st_] - u[o + 2 * st_]) + 27.0 * (u[o + st_] - u[o]) : u[o + st_] - u[o];
+      };
+      const size_t sz = (size_t)N * N;
+      for (int e = tid; e < nzf * nn + S * ng * Ni + S * Ni * ng; e += nt) {
+        int k, zb, yb, xb;
+        if (e < nzf * nn) {                          // z-faces
+          k = 0;
+          zb = zf0 + e / nn;
+          yb = R + (e % nn) / Ni;
+          xb = R + (e % nn) % Ni;
+        } else if (e < nzf * nn + S * ng * Ni) {     // y-faces
+          const int r = e - nzf * nn;
+          k = 1;
+          zb = zo + r / (ng * Ni);
+          yb = g0 + (r % (ng * Ni)) / Ni;
+          xb = R + (r % (ng * Ni)) % Ni;
+        } else {                                     // x-faces
+          const int r = e - nzf * nn - S * ng * Ni;
+          k = 2;
+          zb = zo + r / (Ni * ng);
+          yb = R + (r % (Ni * ng)) / ng;
+          xb = g0 + (r % (Ni * ng)) % ng;
+        }
+        const size_t o = bidx(zb, yb, xb);
+        const size_t st_ = k == 0 ? sz : (k == 1 ? (size_t)N : 1);
+        const double af = af64[k * cap + o];
+        double* F = fl3 + (size_t)k * 4 * cap;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) F[c * cap + o] = af * fdiff(mi64 + c * cap, o, st_);
+        const double wd = k == 0 ? W1d[yb] * W1d[xb] * fdiff(W1d, zb, 1)
+                                 : (k == 1 ? W1d[zb] * W1d[xb] * fdiff(W1d, yb, 1) : W1d[zb] * W1d[yb] * fdiff(W1d, xb, 1));
+        F[3 * cap + o] = af * wd;
+      }
+      __syncthreads();
+      auto fcomb = [](const double* F, size_t o, size_t st_) {
+        return R == 3 ? (F[o - 2 * st_] - F[o + st_]) + 27.0 * (F[o] - F[o - st_]) : F[o] - F[o - st_];
+      };
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
       for (int e = tid; e < S * nn; e += nt) {
         const int z = e / nn, yx = e - z * nn, y = yx / Ni, x = yx - y * Ni;
-        const int idx = (int)bidx(r0 + z + R, y + R, x + R);
-        double H[3];
-        stencil_H<D, R, double>(mi64, af64, cap, st, idx, cs64, H);
+        const size_t idx = bidx(r0 + z + R, y + R, x + R);
+        double H[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          H[c] = (fcomb(fl3 + c * cap, idx, sz) + fcomb(fl3 + (4 + c) * cap, idx, (size_t)N) +
+                  fcomb(fl3 + (8 + c) * cap, idx, 1)) * cs64;
         const double W = W1d[r0 + z + R] * W1d[y + R] * W1d[x + R];
         s0 += W * H[0];
         s1 += W * H[1];
@@ -340,30 +390,7 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         const int io = z * d.PI + y * d.LDI + x;
 #pragma unroll
         for (int c = 0; c < 3; ++c) hiS[c * d.Sc * d.PI + io] = (float)H[c];
-        // H(W) with the same operator (W vanishes on and near the ring)
-        double hwd = 0.0;
-#pragma unroll 1
-        for (int k = 0; k < D; ++k) {
-          const int s = st.s[k];
-          const double* af = af64 + k * cap;
-          double Wv[7];
-#pragma unroll
-          for (int o = -R; o <= R; ++o) {
-            const int id = idx + o * s;
-            const int zb = id / (N * N), rem = id - zb * N * N, yb = rem / N, xb = rem - yb * N;
-            Wv[o + R] = W1d[zb] * W1d[yb] * W1d[xb];
-          }
-          if (R == 1) {
-            hwd += af[idx] * (Wv[2] - Wv[1]) - af[idx - s] * (Wv[1] - Wv[0]);
-          } else {
-            const double g_2 = (Wv[0] - Wv[3]) + 27.0 * (Wv[2] - Wv[1]);
-            const double g_1 = (Wv[1] - Wv[4]) + 27.0 * (Wv[3] - Wv[2]);
-            const double g0 = (Wv[2] - Wv[5]) + 27.0 * (Wv[4] - Wv[3]);
-            const double g1 = (Wv[3] - Wv[6]) + 27.0 * (Wv[5] - Wv[4]);
-            hwd += (af[idx - 2 * s] * g_2 - af[idx + s] * g1) + 27.0 * (af[idx] * g0 - af[idx - s] * g_1);
-          }
-        }
-        hwS[io] = (float)(hwd * cs64);
+        hwS[io] = (float)H[3];
       }
       block_sum3(s0, s1, s2, red);
       if (tid == 0) {
