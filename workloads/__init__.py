@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "CoefTerm", "HMMConfig", "config", "CONFIG_NAMES", "fourier_field",
     "ex1_initial", "ex2_initial", "c1_initial", "uneven_eps_and_n",
-    "macro_coords",
+    "macro_coords", "DNSConfig", "dns_config", "DNS_NAMES", "dns_initial",
 ]
 
 # Coefficient factor kinds and variable scales (per axis of a term).
@@ -335,4 +335,105 @@ def initial_field(cfg: HMMConfig, seed: Optional[int] = None) -> np.ndarray:
         base = 20210820
         s = base + (CONFIG_NAMES.index(cfg.name) if cfg.name in CONFIG_NAMES else 7)
         m = fourier_field(cfg, s if seed is None else seed)
+    return np.ascontiguousarray(m.reshape(3, -1))
+
+
+# --------------------------------------------------------------------------
+# Direct simulation resolving eps (the paper's reference solutions, Section 5)
+# --------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class DNSConfig:
+    """Parameters of a direct simulation of eq. prob on a grid that resolves eps
+    (the fields of the C struct hmm_dns_params).
+
+    dim, n, L        periodic domain [0, L]^dim, n points per axis, dx = L/n
+    alpha            damping (0 <= alpha <= 1)
+    c0, terms, eps   a(x) = c0 + sum(terms), fast variable x/eps
+    coef_fn          a coefficient that is not a sum of separable terms (tabulated
+                     at the faces for the library); replaces c0 + terms when set
+    dt, dt_safety    time step (<= 0: dt_safety times the MPEA stability step)
+    stencil_order    2 or 4
+    precision        0: FP64 state and arithmetic, 1: float-float state, FP32 arithmetic
+    """
+    dim: int
+    n: Sequence[int]
+    alpha: float
+    c0: float
+    terms: List[CoefTerm]
+    eps: float
+    L: float = 1.0
+    dt: float = 0.0
+    dt_safety: float = 0.5
+    stencil_order: int = 4
+    precision: int = 0
+    coef_fn: Optional[Callable] = None
+    name: str = ""
+
+    @property
+    def n_points(self) -> int:
+        return int(np.prod([int(v) for v in list(self.n)[: self.dim]]))
+
+    @property
+    def shape(self):
+        return tuple(int(v) for v in list(self.n)[: self.dim])
+
+    def replace(self, **kw) -> "DNSConfig":
+        return dataclasses.replace(self, **kw)
+
+
+DNS_NAMES = ("dns_loc1d", "dns_quasi2d", "dns_loc2d")
+
+
+def dns_config(name: str, **over) -> DNSConfig:
+    """Named direct simulations of Section 5 (grid sizes as the paper states them).
+
+    dns_loc1d    eq. loc: a = 1.1 + 0.25 sin(2 pi x + 1.1) + 0.5 sin(2 pi x/eps),
+                 eps = 1/400, alpha = 0.01, dx = 1/6000 (15 points per eps)
+    dns_quasi2d  eq. coeff_quasi: a = (1 + 0.25 sin(2 pi x1/eps))(1 + 0.25 sin(2 pi x2/eps)
+                 + 0.25 sin(2 pi 1.41 x2/eps)), expanded into six separable terms,
+                 eps = 0.01, alpha = 0.01, dx = 1/1500
+    dns_loc2d    eq. coeff_loc2D (tabulated), eps = 0.01, alpha = 0.1; the paper does
+                 not state its dx; 15 points per eps as in the other two (dx = 1/1500)
+    """
+    if name == "dns_loc1d":
+        cfg = DNSConfig(dim=1, n=(6000, 1, 1), alpha=0.01, c0=1.1,
+                        terms=[_term(0.25, _sin(0, SCALE_SLOW, 1.0, 1.1)), _term(0.5, _sin(0))],
+                        eps=1.0 / 400, name=name)
+    elif name == "dns_quasi2d":
+        r = 1.41
+        cfg = DNSConfig(dim=2, n=(1500, 1500, 1), alpha=0.01, c0=1.0,
+                        terms=[_term(0.25, _sin(1)), _term(0.25, _sin(1, omega=r)),
+                               _term(0.25, _sin(0)), _term(0.0625, _sin(0), _sin(1)),
+                               _term(0.0625, _sin(0), _sin(1, omega=r))],
+                        eps=0.01, name=name)
+    elif name == "dns_loc2d":
+        cfg = DNSConfig(dim=2, n=(1500, 1500, 1), alpha=0.1, c0=1.0, terms=[], eps=0.01,
+                        coef_fn=coeff_loc2d, name=name)
+    else:
+        raise KeyError(name)
+    return dataclasses.replace(cfg, **over)
+
+
+def dns_coords(cfg: DNSConfig) -> List[np.ndarray]:
+    """Grid nodes x_j = j L/n per axis."""
+    return [np.arange(n) * (cfg.L / n) for n in cfg.shape]
+
+
+def dns_initial(cfg: DNSConfig, noise: float = 0.0, seed: int = 20210820) -> np.ndarray:
+    """Initial data (3, prod n) on the grid: (EX1) in 1D, (EX2) in 2D, as in the
+    paper's direct simulations; ``noise`` > 0 adds seeded N(0, noise^2) values to
+    every component before normalisation (rough data for parity tests)."""
+    X = np.meshgrid(*dns_coords(cfg), indexing="ij")
+    if cfg.dim == 1:
+        mt = ex1_initial(X[0])
+    elif cfg.dim == 2:
+        mt = ex2_initial_unnormalised(X[0], X[1])
+    else:
+        raise ValueError("direct simulations are defined for d = 1 and 2")
+    if noise > 0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        mt = mt + noise * rng.standard_normal(mt.shape)
+    m = mt / np.sqrt((mt ** 2).sum(0))
     return np.ascontiguousarray(m.reshape(3, -1))
