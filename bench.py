@@ -374,6 +374,76 @@ def run_micro_only(args, local_rank):
     print(json.dumps(rec), flush=True)
 
 
+# ---------------------------------------------------------------- direct simulation
+DNS_WORKLOAD = "dns_quasi2d"
+DNS_BYTES_PER_PT = {"fp32": 84.0, "fp64": 120.0}   # algorithmic bytes per point-step
+
+
+def dns_measure(workload=DNS_WORKLOAD, precision="fp32", steps=1000, warmup=50, grid=None):
+    """Time hmm_dns_step on a named direct simulation: ``warmup`` steps (the
+    RK4P start-up and the first MPEA steps), then ``steps`` MPEA steps in one
+    call, timed by the library's events on its stream. Inputs are resident in
+    HBM; the per-step working set (state, history) is larger than L2 at 1500^2
+    (189 MB in the float-float form). Returns a dict."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2108_09463_gb300 import DNS
+    over = {}
+    if grid:
+        over["n"] = tuple(list(grid) + [1] * (3 - len(grid)))
+    cfg = W.dns_config(workload, **over)
+    prec = 0 if precision == "fp64" else 1
+    table = None
+    if cfg.coef_fn is not None:
+        X = W.dns_coords(cfg)
+        dxs = [cfg.L / n for n in cfg.shape]
+        blocks = []
+        for k in range(cfg.dim):
+            P = np.meshgrid(*[x + (0.5 * dxs[a] if a == k else 0.0) for a, x in enumerate(X)], indexing="ij")
+            blocks.append(np.asarray(cfg.coef_fn(P, cfg.eps), dtype=np.float64).ravel())
+        table = np.concatenate(blocks)
+    d = DNS(cfg, precision=prec, face_table=table)
+    M = torch.from_numpy(W.dns_initial(cfg)).cuda()
+    d.step(M, warmup)
+    d.step(M, steps)
+    ms = d.info()["last_ms"]
+    info = d.info()
+    d.close()
+    G = cfg.n_points
+    ms_step = ms / steps
+    return {"workload": workload, "grid": list(cfg.shape), "precision": precision, "steps": steps,
+            "ms_per_step": ms_step, "value": G / (ms_step / 1e3), "unit": "point-steps/s",
+            "dt": info["dt"], "bytes_per_point_step": DNS_BYTES_PER_PT[precision],
+            "achieved_gbs": DNS_BYTES_PER_PT[precision] * G / (ms_step / 1e3) / 1e9,
+            "finite": bool(torch.isfinite(M).all())}
+
+
+def run_dns(args, local_rank):
+    """--dns: one JSON line for the direct simulation (float-float FP32 form and
+    the FP64 form on the same grid)."""
+    import torch
+    from paper_2108_09463_gb300 import build
+    build()
+    torch.cuda.set_device(local_rank)
+    wl = args.workload if args.workload.startswith("dns_") else DNS_WORKLOAD
+    rec = {"mode": "dns"}
+    with ClockSampler(local_rank) as clk:
+        r32 = dns_measure(wl, "fp32", args.steps, args.warmup, args.macro_grid)
+        r64 = dns_measure(wl, "fp64", max(1, args.fp64_steps), args.warmup, args.macro_grid) if args.fp64_steps > 0 else None
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    rec.update(r32)
+    rec["roofline"] = {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                       "frac": r32["achieved_gbs"] / hbm, "traffic": None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+    if r64:
+        rec["fp64"] = r64
+        rec["speedup_vs_fp64"] = r32["value"] / r64["value"]
+    rec["clocks"] = clk.summary()
+    print(json.dumps(rec), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -428,15 +498,20 @@ def main():
     ap.add_argument("--micro-stepper", type=int, default=0, help="with --micro-only: 0 HeunP, 1 RK4P")
     ap.add_argument("--cpu-baseline-micro", action="store_true",
                     help="with --micro-only: also time the oracle on a sample of the boxes")
+    ap.add_argument("--dns", action="store_true",
+                    help="time the direct simulation (--workload dns_*, --macro-grid for its grid, "
+                         "--steps MPEA steps, --fp64-steps for the FP64 form)")
     ap.add_argument("--macro-steps", type=int, default=0,
                     help="with --micro-only: also time this many steady-state macro steps")
     args = ap.parse_args()
-    if args.warmup < 3 and not args.micro_only:
+    if args.warmup < 3 and not (args.micro_only or args.dns):
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.micro_only:
+    if args.dns:
+        run_dns(args, local_rank)
+    elif args.micro_only:
         run_micro_only(args, local_rank)
     elif args.impl == "reference":
         run_reference(args, rank, world)

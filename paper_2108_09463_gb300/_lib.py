@@ -24,6 +24,9 @@ EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_st
             "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
             "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
             "hmm_last_error", "hmm_destroy")
+# The symbols include/hmm_dns.h declares.
+EXPORTED_DNS = ("hmm_dns_init", "hmm_dns_set_face_table", "hmm_dns_step", "hmm_dns_step_host",
+                "hmm_dns_reset", "hmm_dns_info", "hmm_dns_last_error", "hmm_dns_destroy")
 
 
 class HmmCoefTerm(ctypes.Structure):
@@ -40,6 +43,13 @@ class HmmParams(ctypes.Structure):
                 ("dt_safety", c_double), ("px", c_int), ("qx", c_int), ("pt", c_int), ("qt", c_int),
                 ("interp_order", c_int), ("stencil_order", c_int), ("precision", c_int),
                 ("kernel_variant", c_int), ("micro_stepper", c_int), ("reserved", c_int * 3)]
+
+
+class HmmDnsParams(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int * 3), ("L", c_double), ("alpha", c_double),
+                ("dt", c_double), ("dt_safety", c_double), ("c0", c_double), ("n_terms", c_int),
+                ("terms", POINTER(HmmCoefTerm)), ("eps", c_double), ("stencil_order", c_int),
+                ("precision", c_int), ("reserved", c_int * 4)]
 
 
 class HmmError(RuntimeError):
@@ -76,8 +86,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_last_error.restype = c_char_p
     lib.hmm_destroy.argtypes = [c_void_p]
     lib.hmm_destroy.restype = None
-    for name in EXPORTED:
-        if name not in ("hmm_last_error", "hmm_destroy"):
+    lib.hmm_dns_init.argtypes = [POINTER(HmmDnsParams), c_void_p, POINTER(c_void_p)]
+    lib.hmm_dns_set_face_table.argtypes = [c_void_p, c_void_p, c_longlong]
+    lib.hmm_dns_step.argtypes = [c_void_p, c_void_p, c_int]
+    lib.hmm_dns_step_host.argtypes = [c_void_p, c_void_p, c_int]
+    lib.hmm_dns_reset.argtypes = [c_void_p]
+    lib.hmm_dns_info.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]
+    lib.hmm_dns_last_error.argtypes = [c_void_p]
+    lib.hmm_dns_last_error.restype = c_char_p
+    lib.hmm_dns_destroy.argtypes = [c_void_p]
+    lib.hmm_dns_destroy.restype = None
+    for name in EXPORTED + EXPORTED_DNS:
+        if name not in ("hmm_last_error", "hmm_destroy", "hmm_dns_last_error", "hmm_dns_destroy"):
             getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -130,6 +150,39 @@ def make_params(cfg, precision=None, kernel_variant=0):
     p.kernel_variant = int(kernel_variant)
     p.micro_stepper = int(getattr(cfg, "micro_stepper", 0))
     return p, keep
+
+
+def _fill_terms(cfg):
+    terms = (HmmCoefTerm * max(1, len(cfg.terms)))()
+    for i, t in enumerate(cfg.terms):
+        terms[i].amp = float(t.amp)
+        for k in range(3):
+            terms[i].kind[k] = int(t.kind[k]) if k < cfg.dim else 0
+            terms[i].scale[k] = int(t.scale[k])
+            terms[i].omega[k] = float(t.omega[k])
+            terms[i].phase[k] = float(t.phase[k])
+    return terms
+
+
+def make_dns_params(cfg, precision=None):
+    """Fill HmmDnsParams from a problem description (an object with DNSConfig's
+    fields). Returns (params, keepalive)."""
+    terms = _fill_terms(cfg)
+    p = HmmDnsParams()
+    p.dim = int(cfg.dim)
+    for k in range(3):
+        p.n[k] = int(list(cfg.n)[k]) if k < len(cfg.n) else 1
+    p.L = float(cfg.L)
+    p.alpha = float(cfg.alpha)
+    p.dt = float(cfg.dt)
+    p.dt_safety = float(cfg.dt_safety)
+    p.c0 = float(cfg.c0)
+    p.n_terms = len(cfg.terms)
+    p.terms = ctypes.cast(terms, POINTER(HmmCoefTerm))
+    p.eps = float(cfg.eps)
+    p.stencil_order = int(cfg.stencil_order)
+    p.precision = int(cfg.precision if precision is None else precision)
+    return p, [terms]
 
 
 def _ptr(t) -> int:
@@ -256,3 +309,69 @@ def micro_batch_noalloc(cfg, M, out, stream=None):
     if st != HMM_OK:
         raise HmmError(st, lib.hmm_last_error(None).decode())
     return out
+
+
+class DNS:
+    """One direct simulation resolving eps on the current CUDA device (a handle
+    of include/hmm_dns.h). ``face_table``: d blocks of G positive face values
+    for coefficients that are not separable sums (see hmm_dns_set_face_table)."""
+
+    def __init__(self, cfg, precision=None, stream=None, face_table=None):
+        import torch
+        self.lib = load_library()
+        self.cfg = cfg
+        self.G = int(cfg.n_points)
+        params, keep = make_dns_params(cfg, precision)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = c_void_p()
+        st = self.lib.hmm_dns_init(ctypes.byref(params), c_void_p(stream.cuda_stream), ctypes.byref(h))
+        del keep
+        if st != HMM_OK:
+            raise HmmError(st, self.lib.hmm_dns_last_error(None).decode())
+        self.h = h
+        if face_table is not None:
+            self.set_face_table(face_table)
+
+    def _check(self, st):
+        if st != HMM_OK:
+            raise HmmError(st, self.lib.hmm_dns_last_error(self.h).decode())
+
+    def set_face_table(self, table):
+        import numpy as np
+        t = np.ascontiguousarray(table, dtype=np.float64)
+        self._check(self.lib.hmm_dns_set_face_table(self.h, t.ctypes.data, int(t.size)))
+
+    def step(self, M, n_steps=1):
+        """n_steps steps in place on M, a contiguous float64 CUDA tensor (3, G)."""
+        import torch
+        if not (isinstance(M, torch.Tensor) and M.is_cuda and M.dtype == torch.float64
+                and M.is_contiguous() and tuple(M.shape) == (3, self.G)):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of shape (3, {self.G})")
+        self._check(self.lib.hmm_dns_step(self.h, c_void_p(M.data_ptr()), int(n_steps)))
+        return M
+
+    def step_host(self, M, n_steps=1):
+        """As step with M a contiguous float64 host array/tensor (3, G)."""
+        self._check(self.lib.hmm_dns_step_host(self.h, c_void_p(_ptr(M)), int(n_steps)))
+        return M
+
+    def reset(self):
+        self._check(self.lib.hmm_dns_reset(self.h))
+
+    def info(self):
+        dt, j, ms = c_double(), c_longlong(), c_double()
+        self._check(self.lib.hmm_dns_info(self.h, ctypes.byref(dt), ctypes.byref(j), ctypes.byref(ms)))
+        return dict(dt=dt.value, j=int(j.value), last_ms=ms.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hmm_dns_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

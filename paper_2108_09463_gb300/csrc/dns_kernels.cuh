@@ -1,0 +1,312 @@
+// Kernels of the direct simulation resolving eps (include/hmm_dns.h).
+//
+// One warp owns a strip of W = 32 - 2R consecutive nodes of the fast axis
+// (R = 1 for order 2, 3 for order 4) and marches down a chunk of rows of the
+// slow axis. Lane l holds the node x_l = X0 - R + l of the current row (lanes
+// 0..R-1 and 32-R..31 are the strip's halo, taken modulo n with the periodic
+// wrap). Along the fast axis the staggered differences take their neighbours
+// from the other lanes by warp shuffles; along the slow axis each lane keeps
+// its own column's last R+1 rows and the last R+1 face fluxes in registers, so
+// a node's y-divergence is complete R rows after it was loaded. Nothing goes
+// through shared memory and no barrier wider than the warp is needed. Every
+// node is read once per chunk (plus 2R halo rows per chunk and the 2R halo
+// lanes per strip, which the L2 serves).
+//
+// Face fluxes F_f = a_f * G_f with the raw differences
+//   order 4: G_f = (u_{f-1} - u_{f+2}) + 27 (u_{f+1} - u_f),   H += c ((F_{x-2} - F_{x+1}) + 27 (F_x - F_{x-1}))
+//   order 2: G_f = u_{f+1} - u_f,                               H += c (F_x - F_{x-1})
+// (face f between nodes f and f+1), c = 1/(24 dx)^2 or 1/dx^2 per axis.
+//
+// In the float-float form (FF) a node is (hi, lo) per component; each
+// difference is taken on hi and on lo separately and summed, so that it keeps
+// FP32 accuracy relative to its own size instead of to |m|.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+namespace hmm_dns {
+
+constexpr int kMaxTerms = 8;
+constexpr int kWarps = 4;           // warps per block (one work item each)
+constexpr int kErrNonFinite = 1;
+
+enum Mode { kField = 0, kMpea64 = 1, kMpeaFF = 2 };
+
+struct Args {
+  int n0, n1;            // slow-axis rows (1 for d = 1) and fast-axis columns
+  long long G;           // n0 * n1
+  int strips, chunk, chunks, items;
+  double cx, cy;         // stencil scale along the fast and the slow axis
+  int nt;                // separable terms (0 with a face table)
+  double c0;
+  // separable tables: fast axis [nt][n1] (faces with amp folded in, nodes with
+  // amp folded in), slow axis [n0][kMaxTerms] (faces, nodes), FP64 and FP32
+  const double* tfx; const double* tnx; const double* tfy; const double* tny;
+  const float* sfx; const float* snx; const float* sfy; const float* sny;
+  // face tables (TAB): faces along the fast axis and along the slow axis, G each
+  const double* ax64; const double* ay64;
+  const float* ax32; const float* ay32;
+  double alpha, half_dt;
+  // state
+  const double* m64; double* m64_out;                 // kField / kMpea64: 3 x G
+  const float* ff; float* ff_out;                     // kMpeaFF: 6 x G (hi 0..2, lo 3..5)
+  const void* h1; const void* h2; void* h_out;        // history (double or float, 3 x G)
+  double* H_out;                                      // kField: 3 x G
+  int* err;
+};
+
+template <bool FF> struct Node;
+template <> struct Node<false> { double v[3]; };
+template <> struct Node<true> { float hi[3]; float lo[3]; };
+
+template <typename T>
+__device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+template <typename T>
+__device__ __forceinline__ T shfl_dn(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+template <bool FF>
+__device__ __forceinline__ Node<FF> node_shfl_up(const Node<FF>& a, int d) {
+  Node<FF> r;
+  if constexpr (FF) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { r.hi[c] = shfl_up(a.hi[c], d); r.lo[c] = shfl_up(a.lo[c], d); }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r.v[c] = shfl_up(a.v[c], d);
+  }
+  return r;
+}
+
+template <bool FF>
+__device__ __forceinline__ Node<FF> node_shfl_dn(const Node<FF>& a, int d) {
+  Node<FF> r;
+  if constexpr (FF) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { r.hi[c] = shfl_dn(a.hi[c], d); r.lo[c] = shfl_dn(a.lo[c], d); }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r.v[c] = shfl_dn(a.v[c], d);
+  }
+  return r;
+}
+
+// Raw face difference of component c: order 4 from (u_{f-1}, u_f, u_{f+1}, u_{f+2}),
+// order 2 from (u_f, u_{f+1}) passed as (b, c1).
+template <int ORDER, bool FF>
+__device__ __forceinline__ auto face_diff(const Node<FF>& a, const Node<FF>& b, const Node<FF>& c1,
+                                          const Node<FF>& d, int c) {
+  if constexpr (FF) {
+    if constexpr (ORDER == 4) {
+      float gh = (a.hi[c] - d.hi[c]) + 27.0f * (c1.hi[c] - b.hi[c]);
+      float gl = (a.lo[c] - d.lo[c]) + 27.0f * (c1.lo[c] - b.lo[c]);
+      return gh + gl;
+    } else {
+      return (c1.hi[c] - b.hi[c]) + (c1.lo[c] - b.lo[c]);
+    }
+  } else {
+    if constexpr (ORDER == 4) return (a.v[c] - d.v[c]) + 27.0 * (c1.v[c] - b.v[c]);
+    else return c1.v[c] - b.v[c];
+  }
+}
+
+template <bool FF>
+__device__ __forceinline__ Node<FF> load_node(const Args& A, long long idx) {
+  Node<FF> r;
+  if constexpr (FF) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r.hi[c] = __ldg(A.ff + c * A.G + idx);
+      r.lo[c] = __ldg(A.ff + (3 + c) * A.G + idx);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r.v[c] = __ldg(A.m64 + c * A.G + idx);
+  }
+  return r;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// x-part of H at the lane's node (raw, unscaled) from the row's nodes `u`.
+// Returns the divergence of the face fluxes; valid on lanes R..31-R.
+template <int ORDER, bool FF, typename R_>
+__device__ __forceinline__ void x_part(const Node<FF>& u, R_ ax, R_ out[3]) {
+  Node<FF> um1, up1, up2;
+  if constexpr (ORDER == 4) {
+    um1 = node_shfl_up<FF>(u, 1);
+    up1 = node_shfl_dn<FF>(u, 1);
+    up2 = node_shfl_dn<FF>(u, 2);
+  } else {
+    up1 = node_shfl_dn<FF>(u, 1);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R_ F = ax * face_diff<ORDER, FF>(um1, u, up1, up2, c);
+    if constexpr (ORDER == 4) {
+      R_ Fm2 = shfl_up(F, 2), Fm1 = shfl_up(F, 1), Fp1 = shfl_dn(F, 1);
+      out[c] = (Fm2 - Fp1) + R_(27) * (F - Fm1);
+    } else {
+      R_ Fm1 = shfl_up(F, 1);
+      out[c] = F - Fm1;
+    }
+  }
+}
+
+template <int ORDER, bool TWO_D, bool TAB, int MODE>
+__global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
+  constexpr bool FF = (MODE == kMpeaFF);
+  using R_ = typename std::conditional<FF, float, double>::type;
+  constexpr int RR = (ORDER == 4) ? 3 : 1;
+  constexpr int W = 32 - 2 * RR;
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (item >= A.items) return;                      // whole warp leaves together
+  const int strip = item % A.strips;
+  const int chunk = item / A.strips;
+  const int n0 = A.n0, n1 = A.n1;
+  int xl = strip * W - RR + lane;                   // lane's node on the fast axis
+  const bool out_lane = lane >= RR && lane < 32 - RR && xl < n1;
+  xl = (xl % n1 + n1) % n1;
+  const int r0 = TWO_D ? chunk * A.chunk : 0;
+  const int r1 = TWO_D ? min(r0 + A.chunk, n0) : 1;
+
+  // per-lane separable factors of the fast axis (amp folded in)
+  R_ fx[kMaxTerms], nx[kMaxTerms];
+  if constexpr (!TAB) {
+#pragma unroll
+    for (int t = 0; t < kMaxTerms; ++t) {
+      if (t < A.nt) {
+        if constexpr (FF) { fx[t] = __ldg(A.sfx + t * n1 + xl); nx[t] = __ldg(A.snx + t * n1 + xl); }
+        else { fx[t] = __ldg(A.tfx + t * n1 + xl); nx[t] = __ldg(A.tnx + t * n1 + xl); }
+      } else {
+        fx[t] = R_(0); nx[t] = R_(0);
+      }
+    }
+  }
+  auto coef = [&](const R_* fac, const void* rowtab, int row) -> R_ {
+    const R_* rt = reinterpret_cast<const R_*>(rowtab) + (long long)row * kMaxTerms;
+    R_ a = R_(A.c0);
+#pragma unroll
+    for (int t = 0; t < kMaxTerms; ++t)
+      if (t < A.nt) a += fac[t] * __ldg(rt + t);
+    return a;
+  };
+
+  Node<FF> win[RR + 1];     // own column, rows q-R..q
+  R_ fq[RR + 1][3];         // y-face fluxes, oldest first
+  const int q_lo = TWO_D ? r0 - RR : 0;
+  const int q_hi = TWO_D ? r1 - 1 + RR : 0;
+  for (int q = q_lo; q <= q_hi; ++q) {
+    const int row = TWO_D ? ((q % n0) + n0) % n0 : 0;
+    const long long base = (long long)row * n1;
+#pragma unroll
+    for (int k = 0; k < RR; ++k) win[k] = win[k + 1];
+    win[RR] = load_node<FF>(A, base + xl);
+    if constexpr (TWO_D) {
+      if (q < r0) continue;                         // window not full yet
+      // y-face between rows q-R+... : order 4 face (q-2), order 2 face (q-1)
+      const int frow_raw = (ORDER == 4) ? q - 2 : q - 1;
+      const int frow = ((frow_raw % n0) + n0) % n0;
+      R_ ay;
+      if constexpr (TAB) ay = FF ? R_(__ldg(A.ay32 + (long long)frow * n1 + xl)) : R_(__ldg(A.ay64 + (long long)frow * n1 + xl));
+      else ay = coef(nx, FF ? (const void*)A.sfy : (const void*)A.tfy, frow);
+#pragma unroll
+      for (int k = 0; k < RR; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fq[k][c] = fq[k + 1][c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (ORDER == 4) fq[RR][c] = ay * face_diff<4, FF>(win[0], win[1], win[2], win[3], c);
+        else fq[RR][c] = ay * face_diff<2, FF>(win[0], win[0], win[1], win[1], c);
+      }
+      if (q < r0 + RR) continue;                    // face queue not full yet
+    }
+    // the node row p = q - R (2D) or the only row (1D) is complete
+    const int p = TWO_D ? q - RR : 0;               // p in [r0, r1): no wrap
+    const Node<FF>& u = TWO_D ? win[0] : win[RR];   // 1D: the row just loaded
+    R_ ax;
+    if constexpr (TAB) ax = FF ? R_(__ldg(A.ax32 + (long long)p * n1 + xl)) : R_(__ldg(A.ax64 + (long long)p * n1 + xl));
+    else ax = coef(fx, FF ? (const void*)A.sny : (const void*)A.tny, p);
+    R_ H[3];
+    x_part<ORDER, FF, R_>(u, ax, H);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      R_ hy = R_(0);
+      if constexpr (TWO_D) {
+        if constexpr (ORDER == 4) hy = (fq[0][c] - fq[3][c]) + R_(27) * (fq[2][c] - fq[1][c]);
+        else hy = fq[1][c] - fq[0][c];
+      }
+      H[c] = R_(A.cx) * H[c] + R_(A.cy) * hy;
+    }
+    if (!out_lane) continue;
+    const long long gi = (long long)p * n1 + xl;
+    const long long G = A.G;
+    if constexpr (MODE == kField) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.H_out[c * G + gi] = H[c];
+    } else {
+      R_ m[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (FF) m[c] = u.hi[c];
+        else m[c] = u.v[c];
+      }
+      const R_ al = R_(A.alpha);
+      // h^j = H + alpha m x H (eq. h_term)
+      R_ h[3];
+      h[0] = H[0] + al * (m[1] * H[2] - m[2] * H[1]);
+      h[1] = H[1] + al * (m[2] * H[0] - m[0] * H[2]);
+      h[2] = H[2] + al * (m[0] * H[1] - m[1] * H[0]);
+      const R_* H1 = reinterpret_cast<const R_*>(A.h1);
+      const R_* H2 = reinterpret_cast<const R_*>(A.h2);
+      R_* HO = reinterpret_cast<R_*>(A.h_out);
+      const R_ c23 = R_(23.0 / 12.0), c16 = R_(16.0 / 12.0), c5 = R_(5.0 / 12.0);
+      R_ w[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        R_ hh = (c23 * h[c] - c16 * __ldg(H1 + c * G + gi)) + c5 * __ldg(H2 + c * G + gi);
+        w[c] = R_(A.half_dt) * hh;
+        HO[c * G + gi] = h[c];
+      }
+      // midpoint update (eq. mpe_update) in closed form
+      R_ a0 = w[1] * m[2] - w[2] * m[1];
+      R_ a1 = w[2] * m[0] - w[0] * m[2];
+      R_ a2 = w[0] * m[1] - w[1] * m[0];
+      R_ b0 = w[1] * a2 - w[2] * a1;
+      R_ b1 = w[2] * a0 - w[0] * a2;
+      R_ b2 = w[0] * a1 - w[1] * a0;
+      R_ f = R_(2) / (R_(1) + (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+      R_ dl[3] = {f * (a0 + b0), f * (a1 + b1), f * (a2 + b2)};
+      bool bad = false;
+      if constexpr (FF) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float s, e;
+          two_sum(u.hi[c], dl[c], s, e);
+          float lo = u.lo[c] + e;
+          float hi = s + lo;
+          lo = lo - (hi - s);
+          A.ff_out[c * G + gi] = hi;
+          A.ff_out[(3 + c) * G + gi] = lo;
+          bad |= !isfinite(hi);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double v = u.v[c] + dl[c];
+          A.m64_out[c * G + gi] = v;
+          bad |= !isfinite(v);
+        }
+      }
+      if (bad) atomicOr(A.err, kErrNonFinite);
+    }
+  }
+}
+
+}  // namespace hmm_dns

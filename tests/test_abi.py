@@ -1,6 +1,6 @@
 """CPU checks of the C ABI: the library loads, exports every entry point that
-include/hmm.h declares, and rejects invalid parameters on the host (no GPU
-needed: validation happens before any CUDA call)."""
+include/hmm.h and include/hmm_dns.h declare, and rejects invalid parameters on
+the host (no GPU needed: validation happens before any CUDA call)."""
 import ctypes
 import os
 import re
@@ -19,8 +19,8 @@ def lib():
     return load_library()
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "hmm.h")).read()
+def _declared(header="hmm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(hmm_[a-z_0-9]+)\s*\(", src)))
 
@@ -31,6 +31,23 @@ def test_exports_every_declared_symbol(lib):
     assert decl == sorted(EXPORTED)
     for name in decl:
         assert hasattr(lib, name), name
+
+
+def test_exports_every_declared_dns_symbol(lib):
+    from paper_2108_09463_gb300 import EXPORTED_DNS
+    decl = _declared("hmm_dns.h")
+    assert decl == sorted(EXPORTED_DNS)
+    for name in decl:
+        assert hasattr(lib, name), name
+
+
+def test_headers_cover_every_export():
+    """Every .h under include/ is bound: no header declares an unbound symbol."""
+    from paper_2108_09463_gb300 import EXPORTED, EXPORTED_DNS
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        names |= set(_declared(f))
+    assert names == set(EXPORTED) | set(EXPORTED_DNS)
 
 
 def _struct_fields(src, name):
@@ -53,6 +70,13 @@ def test_struct_layout_matches_header():
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     assert [f[0] for f in HmmParams._fields_] == _struct_fields(src, "hmm_params")
     assert [f[0] for f in HmmCoefTerm._fields_] == _struct_fields(src, "hmm_coef_term")
+
+
+def test_dns_struct_layout_matches_header():
+    from paper_2108_09463_gb300._lib import HmmDnsParams
+    src = open(os.path.join(ROOT, "include", "hmm_dns.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    assert [f[0] for f in HmmDnsParams._fields_] == _struct_fields(src, "hmm_dns_params")
 
 
 def _init(lib, cfg, **over):
@@ -93,3 +117,45 @@ def test_null_arguments(lib):
     assert lib.hmm_micro_batch(None, None, None) == 7
     assert lib.hmm_macro_step(None, None, 1) == 7
     lib.hmm_destroy(None)
+
+
+def _dns_init(lib, cfg, **over):
+    from paper_2108_09463_gb300._lib import make_dns_params
+    p, keep = make_dns_params(cfg)
+    for k, v in over.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    st = lib.hmm_dns_init(ctypes.byref(p), None, ctypes.byref(h))
+    msg = lib.hmm_dns_last_error(None).decode()
+    if st == 0:
+        lib.hmm_dns_destroy(h)
+    return st, msg
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(dim=3), "dim"), (dict(alpha=-0.1), "alpha"), (dict(alpha=1.5), "alpha"),
+    (dict(stencil_order=3), "stencil_order"), (dict(precision=2), "precision"),
+    (dict(eps=0.0), "eps"), (dict(n_terms=9), "n_terms"), (dict(L=0.0), "L"),
+    (dict(c0=0.2), "a^eps <= 0"),
+])
+def test_dns_invalid_params_rejected_on_host(lib, over, needle):
+    cfg = W.dns_config("dns_quasi2d", n=(40, 36, 1))
+    st, msg = _dns_init(lib, cfg, **over)
+    assert st == 1, (st, msg)
+    assert needle in msg
+
+
+def test_dns_grid_limits(lib):
+    cfg = W.dns_config("dns_quasi2d", n=(3, 36, 1))
+    st, msg = _dns_init(lib, cfg)
+    assert st == 1 and "n[k]" in msg
+    cfg = W.dns_config("dns_quasi2d", n=(1 << 16, 1 << 16, 1))
+    st, msg = _dns_init(lib, cfg)
+    assert st == 1 and "too many" in msg
+
+
+def test_dns_null_arguments(lib):
+    assert lib.hmm_dns_init(None, None, None) == 1
+    assert lib.hmm_dns_step(None, None, 1) == 7
+    assert lib.hmm_dns_reset(None) == 7
+    lib.hmm_dns_destroy(None)
