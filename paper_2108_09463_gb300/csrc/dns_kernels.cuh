@@ -198,38 +198,44 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
     return a;
   };
 
-  Node<FF> win[RR + 1];     // own column, rows q-R..q
-  R_ fq[RR + 1][3];         // y-face fluxes, oldest first
-  const int q_lo = TWO_D ? r0 - RR : 0;
-  const int q_hi = TWO_D ? r1 - 1 + RR : 0;
-  for (int q = q_lo; q <= q_hi; ++q) {
+  // Rolling state of the own column: rows q-R..q and the last R+1 y-face fluxes
+  // (order 4: faces q-5..q-2, order 2: faces q-2..q-1), oldest first.
+  Node<FF> win[RR + 1];
+  R_ fq[RR + 1][3];
+#pragma unroll
+  for (int k = 0; k <= RR; ++k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      fq[k][c] = R_(0);
+      if constexpr (FF) { win[k].hi[c] = 0.f; win[k].lo[c] = 0.f; }
+      else win[k].v[c] = 0.0;
+    }
+  }
+  auto push_row = [&](int q) {
     const int row = TWO_D ? ((q % n0) + n0) % n0 : 0;
-    const long long base = (long long)row * n1;
 #pragma unroll
     for (int k = 0; k < RR; ++k) win[k] = win[k + 1];
-    win[RR] = load_node<FF>(A, base + xl);
-    if constexpr (TWO_D) {
-      if (q < r0) continue;                         // window not full yet
-      // y-face between rows q-R+... : order 4 face (q-2), order 2 face (q-1)
-      const int frow_raw = (ORDER == 4) ? q - 2 : q - 1;
-      const int frow = ((frow_raw % n0) + n0) % n0;
-      R_ ay;
-      if constexpr (TAB) ay = FF ? R_(__ldg(A.ay32 + (long long)frow * n1 + xl)) : R_(__ldg(A.ay64 + (long long)frow * n1 + xl));
-      else ay = coef(nx, FF ? (const void*)A.sfy : (const void*)A.tfy, frow);
+    win[RR] = load_node<FF>(A, (long long)row * n1 + xl);
+  };
+  // y-face flux from the full window: order 4 the face between rows q-2 and q-1
+  // (rows q-3..q), order 2 the face between rows q-1 and q
+  auto push_face = [&](int q) {
+    const int frow = (((ORDER == 4 ? q - 2 : q - 1) % n0) + n0) % n0;
+    R_ ay;
+    if constexpr (TAB) ay = FF ? R_(__ldg(A.ay32 + (long long)frow * n1 + xl)) : R_(__ldg(A.ay64 + (long long)frow * n1 + xl));
+    else ay = coef(nx, FF ? (const void*)A.sfy : (const void*)A.tfy, frow);
 #pragma unroll
-      for (int k = 0; k < RR; ++k)
+    for (int k = 0; k < RR; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) fq[k][c] = fq[k + 1][c];
+      for (int c = 0; c < 3; ++c) fq[k][c] = fq[k + 1][c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if constexpr (ORDER == 4) fq[RR][c] = ay * face_diff<4, FF>(win[0], win[1], win[2], win[3], c);
-        else fq[RR][c] = ay * face_diff<2, FF>(win[0], win[0], win[1], win[1], c);
-      }
-      if (q < r0 + RR) continue;                    // face queue not full yet
+    for (int c = 0; c < 3; ++c) {
+      if constexpr (ORDER == 4) fq[RR][c] = ay * face_diff<4, FF>(win[0], win[1], win[2], win[3], c);
+      else fq[RR][c] = ay * face_diff<2, FF>(win[0], win[0], win[1], win[1], c);
     }
-    // the node row p = q - R (2D) or the only row (1D) is complete
-    const int p = TWO_D ? q - RR : 0;               // p in [r0, r1): no wrap
-    const Node<FF>& u = TWO_D ? win[0] : win[RR];   // 1D: the row just loaded
+  };
+  // H at the lane's node of row p (node values u), then the point's update.
+  auto emit = [&](int p, const Node<FF>& u) {
     R_ ax;
     if constexpr (TAB) ax = FF ? R_(__ldg(A.ax32 + (long long)p * n1 + xl)) : R_(__ldg(A.ax64 + (long long)p * n1 + xl));
     else ax = coef(fx, FF ? (const void*)A.sny : (const void*)A.tny, p);
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
       }
       H[c] = R_(A.cx) * H[c] + R_(A.cy) * hy;
     }
-    if (!out_lane) continue;
+    if (!out_lane) return;
     const long long gi = (long long)p * n1 + xl;
     const long long G = A.G;
     if constexpr (MODE == kField) {
@@ -305,6 +311,24 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
         }
       }
       if (bad) atomicOr(A.err, kErrNonFinite);
+    }
+  };
+
+  if constexpr (!TWO_D) {
+    push_row(0);
+    emit(0, win[RR]);
+  } else {
+    // rows r0-R..r0-1 fill the window; rows r0..r0+R-1 also push their faces;
+    // from row r0+R on each new row completes row p = q - R (p in [r0, r1))
+    for (int q = r0 - RR; q < r0; ++q) push_row(q);
+    for (int q = r0; q < r0 + RR; ++q) {
+      push_row(q);
+      push_face(q);
+    }
+    for (int q = r0 + RR; q < r1 + RR; ++q) {
+      push_row(q);
+      push_face(q);
+      emit(q - RR, win[0]);
     }
   }
 }

@@ -157,6 +157,18 @@ __host__ __device__ inline bool res_setup_fits(const ResDims& d, int N, int inte
 // per CTA: m_init (3), face coefficients (2), x- and y-face fluxes of m_init and W (4 + 4)
 __host__ __device__ inline size_t res2d_arena_doubles(int nmax) { return (size_t)13 * nmax * nmax; }
 
+// Drops the whole 128-byte lines of [p, p + bytes) from L2 without writing them
+// back (discard.global.L2): the CTA's set-up arena is dead once the box's
+// shared-memory tables are built, and the next box's set-up rewrites it. Call
+// between two barriers: the first ends every read of the range, the second
+// orders the discards before any later write to it.
+__device__ __forceinline__ void l2_discard(const void* p, size_t bytes, int tid, int nt) {
+  const unsigned long long b = ((unsigned long long)p + 127ull) & ~127ull;
+  const unsigned long long e = ((unsigned long long)p + bytes) & ~127ull;
+  for (unsigned long long q = b + 128ull * (unsigned long long)tid; q < e; q += 128ull * (unsigned long long)nt)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(q) : "memory");
+}
+
 
 // One persistent launch: its work items, its queue counter and its cluster size.
 struct ResLaunch {
@@ -494,6 +506,8 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         pk[q].s0[1] = s1 * wsum;
         pk[q].s0[2] = s2 * wsum;
       }
+      __syncthreads();
+      l2_discard(mi64, res2d_arena_doubles(a.nmax) * sizeof(double), tid, nt);
       __syncthreads();
     }
     // Neighbouring CTAs write halo rows into this CTA's slabs from stage 1 on: the

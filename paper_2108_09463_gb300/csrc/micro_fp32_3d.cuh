@@ -399,6 +399,8 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         pk[0].s0[2] = s2 * wsum;
       }
       __syncthreads();
+      l2_discard(mi64, res3d_arena_doubles(a.nmax) * sizeof(double), tid, nt);
+      __syncthreads();
     }
     // Addresses of the planes beyond this slab (in the neighbouring CTAs' shared
     // memory; the same layout everywhere) for vA (first half) and vB (second half).
