@@ -176,22 +176,25 @@ __global__ void dns_rk4_stage(int stage, long long G, double alpha, double dt, d
   for (int c = 0; c < 3; ++c) out[c * G + i] = u[c] / nrm;
 }
 
-// FP64 state -> float-float state (hi = fl(m), lo = fl(m - hi)) and back.
-__global__ void dns_split(long long G, const double* M, float* S) {
+// FP64 state -> float-float state (hi = fl(m), lo = fl(m - hi), one float2 per
+// component) and back.
+__global__ void dns_split(long long G, const double* M, float2* S) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= G) return;
   for (int c = 0; c < 3; ++c) {
     double v = M[c * G + i];
     float hi = (float)v;
-    S[c * G + i] = hi;
-    S[(3 + c) * G + i] = (float)(v - (double)hi);
+    S[c * G + i] = make_float2(hi, (float)(v - (double)hi));
   }
 }
 
-__global__ void dns_join(long long G, const float* S, double* M) {
+__global__ void dns_join(long long G, const float2* S, double* M) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= G) return;
-  for (int c = 0; c < 3; ++c) M[c * G + i] = (double)S[c * G + i] + (double)S[(3 + c) * G + i];
+  for (int c = 0; c < 3; ++c) {
+    const float2 v = S[c * G + i];
+    M[c * G + i] = (double)v.x + (double)v.y;
+  }
 }
 
 int pw_blocks(long long G) { return (int)((G + 255) / 256); }
@@ -216,8 +219,29 @@ cudaError_t launch_stencil(int mode, const DnsHandle* h, const Args& a) {
   return h->tab ? launch_mode<2, false, true>(mode, a, h->stream) : launch_mode<2, false, false>(mode, a, h->stream);
 }
 
-// Rows per work item: enough work items for about 64 resident warps per SM
-// on every SM, at least 8 rows (the 2R halo rows are re-read per chunk).
+// Resident warps of the time-stepping kernel on the whole GPU (occupancy of
+// its instantiation times the SM count); 152 * 16 if the device cannot be asked.
+template <int ORDER, bool TWO_D, bool TAB>
+long long resident_warps_of(int mode) {
+  int dev = 0, sms = 0, blocks = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    if (mode == kMpeaFF)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dns_kernel<ORDER, TWO_D, TAB, kMpeaFF>, 32 * kWarps, 0);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dns_kernel<ORDER, TWO_D, TAB, kMpea64>, 32 * kWarps, 0);
+  }
+  if (e != cudaSuccess || sms <= 0 || blocks <= 0) {
+    cudaGetLastError();
+    return 152LL * 16;
+  }
+  return (long long)sms * blocks * kWarps;
+}
+
+// Rows per work item: as few chunks as keep every resident warp of the
+// time-stepping kernel busy in one wave (each chunk re-reads 2R halo rows, so
+// long chunks are cheaper), at least 8 rows.
 void plan_work(DnsHandle* h) {
   const int R = h->order == 4 ? 3 : 1;
   const int W = 32 - 2 * R;
@@ -226,14 +250,14 @@ void plan_work(DnsHandle* h) {
   a.n1 = h->n1;
   a.G = h->G;
   a.strips = (h->n1 + W - 1) / W;
-  int sms = 152;
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->d == 1) {
     a.chunk = 1;
     a.chunks = 1;
   } else {
-    const long long target = (long long)sms * 64;
+    const int mode = h->precision == HMM_FP64_PLAIN ? kMpea64 : kMpeaFF;
+    long long target;
+    if (h->order == 4) target = h->tab ? resident_warps_of<4, true, true>(mode) : resident_warps_of<4, true, false>(mode);
+    else target = h->tab ? resident_warps_of<2, true, true>(mode) : resident_warps_of<2, true, false>(mode);
     long long ch = ((long long)h->n0 * a.strips + target - 1) / target;
     ch = std::max<long long>(8, std::min<long long>(ch, h->n0));
     a.chunk = (int)ch;
@@ -364,8 +388,8 @@ hmm_status enqueue_mpea_step(DnsHandle* h) {
     a.m64_out = (double*)h->d_state[nxt];
     mode = kMpea64;
   } else {
-    a.ff = (const float*)h->d_state[h->cur];
-    a.ff_out = (float*)h->d_state[nxt];
+    a.ff = (const float2*)h->d_state[h->cur];
+    a.ff_out = (float2*)h->d_state[nxt];
     mode = kMpeaFF;
   }
   cudaError_t e = launch_stencil(mode, h, a);
@@ -385,7 +409,7 @@ hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
   double* m64 = ff ? h->d_m64 : (double*)h->d_state[h->cur];
   bool in_m64 = true;
   if (ff && h->j >= 2) {
-    dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, M_dev, (float*)h->d_state[h->cur]);
+    dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, M_dev, (float2*)h->d_state[h->cur]);
     in_m64 = false;
   } else {
     DNS_CUDA(h, cudaMemcpyAsync(m64, M_dev, bytes64, cudaMemcpyDeviceToDevice, h->stream));
@@ -396,7 +420,7 @@ hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
       DNS_TRY(enqueue_rk4_step(h, ff ? h->d_m64 : (double*)h->d_state[h->cur]));
     } else {
       if (ff && in_m64) {
-        dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, h->d_m64, (float*)h->d_state[h->cur]);
+        dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, h->d_m64, (float2*)h->d_state[h->cur]);
         in_m64 = false;
       }
       DNS_TRY(enqueue_mpea_step(h));
@@ -404,7 +428,7 @@ hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
     h->j += 1;
   }
   if (ff && !in_m64) {
-    dns_join<<<pw_blocks(G), 256, 0, h->stream>>>(G, (const float*)h->d_state[h->cur], M_dev);
+    dns_join<<<pw_blocks(G), 256, 0, h->stream>>>(G, (const float2*)h->d_state[h->cur], M_dev);
   } else {
     const double* src = ff ? h->d_m64 : (const double*)h->d_state[h->cur];
     DNS_CUDA(h, cudaMemcpyAsync(M_dev, src, bytes64, cudaMemcpyDeviceToDevice, h->stream));
@@ -544,6 +568,7 @@ hmm_status hmm_dns_set_face_table(void* handle, const double* table_host, long l
   h->base.ax32 = h->d_face32;
   h->base.ay32 = h->d_face32 + G;
   h->tab = true;
+  plan_work(h);
   h->a_max = amax;
   DNS_TRY(pick_dt(h));
   h->j = 0;

@@ -17,9 +17,14 @@
 //   order 2: G_f = u_{f+1} - u_f,                               H += c (F_x - F_{x-1})
 // (face f between nodes f and f+1), c = 1/(24 dx)^2 or 1/dx^2 per axis.
 //
-// In the float-float form (FF) a node is (hi, lo) per component; each
-// difference is taken on hi and on lo separately and summed, so that it keeps
-// FP32 accuracy relative to its own size instead of to |m|.
+// In the float-float form (FF) a node is (hi, lo) per component, stored as one
+// float2 per component; each difference is taken on hi and on lo separately
+// and summed, so that it keeps FP32 accuracy relative to its own size instead
+// of to |m|.
+//
+// Latency hiding: the next row's loads and the output row's history loads are
+// issued before the current row's arithmetic, and the per-lane coefficient
+// factors live in shared memory instead of registers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -51,7 +56,7 @@ struct Args {
   double alpha, half_dt;
   // state
   const double* m64; double* m64_out;                 // kField / kMpea64: 3 x G
-  const float* ff; float* ff_out;                     // kMpeaFF: 6 x G (hi 0..2, lo 3..5)
+  const float2* ff; float2* ff_out;                   // kMpeaFF: 3 x G (hi, lo) pairs
   const void* h1; const void* h2; void* h_out;        // history (double or float, 3 x G)
   double* H_out;                                      // kField: 3 x G
   int* err;
@@ -117,8 +122,9 @@ __device__ __forceinline__ Node<FF> load_node(const Args& A, long long idx) {
   if constexpr (FF) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      r.hi[c] = __ldg(A.ff + c * A.G + idx);
-      r.lo[c] = __ldg(A.ff + (3 + c) * A.G + idx);
+      const float2 v = __ldg(A.ff + c * A.G + idx);
+      r.hi[c] = v.x;
+      r.lo[c] = v.y;
     }
   } else {
 #pragma unroll
@@ -159,13 +165,15 @@ __device__ __forceinline__ void x_part(const Node<FF>& u, R_ ax, R_ out[3]) {
 }
 
 template <int ORDER, bool TWO_D, bool TAB, int MODE>
-__global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
+__global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_kernel(Args A) {
   constexpr bool FF = (MODE == kMpeaFF);
   using R_ = typename std::conditional<FF, float, double>::type;
   constexpr int RR = (ORDER == 4) ? 3 : 1;
   constexpr int W = 32 - 2 * RR;
-  const int lane = threadIdx.x & 31;
-  const int item = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  // per-lane separable factors of the fast axis (amp folded in): faces, nodes
+  __shared__ R_ s_fac[kWarps][2][kMaxTerms][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int item = blockIdx.x * kWarps + wib;
   if (item >= A.items) return;                      // whole warp leaves together
   const int strip = item % A.strips;
   const int chunk = item / A.strips;
@@ -175,26 +183,24 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
   xl = (xl % n1 + n1) % n1;
   const int r0 = TWO_D ? chunk * A.chunk : 0;
   const int r1 = TWO_D ? min(r0 + A.chunk, n0) : 1;
-
-  // per-lane separable factors of the fast axis (amp folded in)
-  R_ fx[kMaxTerms], nx[kMaxTerms];
+  const int nt = A.nt;
   if constexpr (!TAB) {
-#pragma unroll
-    for (int t = 0; t < kMaxTerms; ++t) {
-      if (t < A.nt) {
-        if constexpr (FF) { fx[t] = __ldg(A.sfx + t * n1 + xl); nx[t] = __ldg(A.snx + t * n1 + xl); }
-        else { fx[t] = __ldg(A.tfx + t * n1 + xl); nx[t] = __ldg(A.tnx + t * n1 + xl); }
+    for (int t = 0; t < nt; ++t) {
+      if constexpr (FF) {
+        s_fac[wib][0][t][lane] = __ldg(A.sfx + t * n1 + xl);
+        s_fac[wib][1][t][lane] = __ldg(A.snx + t * n1 + xl);
       } else {
-        fx[t] = R_(0); nx[t] = R_(0);
+        s_fac[wib][0][t][lane] = __ldg(A.tfx + t * n1 + xl);
+        s_fac[wib][1][t][lane] = __ldg(A.tnx + t * n1 + xl);
       }
     }
+    __syncwarp();
   }
-  auto coef = [&](const R_* fac, const void* rowtab, int row) -> R_ {
+  // c0 + sum_t fac_t(lane) * rowtab[row][t] (which = 0: fast-axis faces, 1: nodes)
+  auto coef = [&](int which, const void* rowtab, int row) -> R_ {
     const R_* rt = reinterpret_cast<const R_*>(rowtab) + (long long)row * kMaxTerms;
     R_ a = R_(A.c0);
-#pragma unroll
-    for (int t = 0; t < kMaxTerms; ++t)
-      if (t < A.nt) a += fac[t] * __ldg(rt + t);
+    for (int t = 0; t < nt; ++t) a += s_fac[wib][which][t][lane] * __ldg(rt + t);
     return a;
   };
 
@@ -211,19 +217,29 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
       else win[k].v[c] = 0.0;
     }
   }
+  // q in [r0 - R, r1 + R) and n0 >= 4 > R: one add or subtract wraps it
+  auto wrap = [&](int q) { return q < 0 ? q + n0 : (q >= n0 ? q - n0 : q); };
+  auto load_row = [&](int q) {
+    const int row = TWO_D ? wrap(q) : 0;
+    return load_node<FF>(A, (long long)row * n1 + xl);
+  };
+  // the window takes row q, which `nxt` holds; the load of row q + 1 is issued
+  // at once (when q + 1 <= q_last) so that it is in flight during row q's work
+  const int q_last = TWO_D ? r1 - 1 + RR : 0;
+  Node<FF> nxt = load_row(TWO_D ? r0 - RR : 0);
   auto push_row = [&](int q) {
-    const int row = TWO_D ? ((q % n0) + n0) % n0 : 0;
 #pragma unroll
     for (int k = 0; k < RR; ++k) win[k] = win[k + 1];
-    win[RR] = load_node<FF>(A, (long long)row * n1 + xl);
+    win[RR] = nxt;
+    if (q < q_last) nxt = load_row(q + 1);
   };
   // y-face flux from the full window: order 4 the face between rows q-2 and q-1
   // (rows q-3..q), order 2 the face between rows q-1 and q
   auto push_face = [&](int q) {
-    const int frow = (((ORDER == 4 ? q - 2 : q - 1) % n0) + n0) % n0;
+    const int frow = wrap(ORDER == 4 ? q - 2 : q - 1);
     R_ ay;
     if constexpr (TAB) ay = FF ? R_(__ldg(A.ay32 + (long long)frow * n1 + xl)) : R_(__ldg(A.ay64 + (long long)frow * n1 + xl));
-    else ay = coef(nx, FF ? (const void*)A.sfy : (const void*)A.tfy, frow);
+    else ay = coef(1, FF ? (const void*)A.sfy : (const void*)A.tfy, frow);
 #pragma unroll
     for (int k = 0; k < RR; ++k)
 #pragma unroll
@@ -236,9 +252,21 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
   };
   // H at the lane's node of row p (node values u), then the point's update.
   auto emit = [&](int p, const Node<FF>& u) {
+    const long long gi = (long long)p * n1 + xl;
+    const long long G = A.G;
+    R_ hp1[3], hp2[3];                               // h^{j-1}, h^{j-2}: loads issued first
+    if constexpr (MODE != kField) {
+      const R_* H1 = reinterpret_cast<const R_*>(A.h1);
+      const R_* H2 = reinterpret_cast<const R_*>(A.h2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        hp1[c] = out_lane ? __ldg(H1 + c * G + gi) : R_(0);
+        hp2[c] = out_lane ? __ldg(H2 + c * G + gi) : R_(0);
+      }
+    }
     R_ ax;
     if constexpr (TAB) ax = FF ? R_(__ldg(A.ax32 + (long long)p * n1 + xl)) : R_(__ldg(A.ax64 + (long long)p * n1 + xl));
-    else ax = coef(fx, FF ? (const void*)A.sny : (const void*)A.tny, p);
+    else ax = coef(0, FF ? (const void*)A.sny : (const void*)A.tny, p);
     R_ H[3];
     x_part<ORDER, FF, R_>(u, ax, H);
 #pragma unroll
@@ -251,8 +279,6 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
       H[c] = R_(A.cx) * H[c] + R_(A.cy) * hy;
     }
     if (!out_lane) return;
-    const long long gi = (long long)p * n1 + xl;
-    const long long G = A.G;
     if constexpr (MODE == kField) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.H_out[c * G + gi] = H[c];
@@ -269,14 +295,12 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
       h[0] = H[0] + al * (m[1] * H[2] - m[2] * H[1]);
       h[1] = H[1] + al * (m[2] * H[0] - m[0] * H[2]);
       h[2] = H[2] + al * (m[0] * H[1] - m[1] * H[0]);
-      const R_* H1 = reinterpret_cast<const R_*>(A.h1);
-      const R_* H2 = reinterpret_cast<const R_*>(A.h2);
       R_* HO = reinterpret_cast<R_*>(A.h_out);
       const R_ c23 = R_(23.0 / 12.0), c16 = R_(16.0 / 12.0), c5 = R_(5.0 / 12.0);
       R_ w[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        R_ hh = (c23 * h[c] - c16 * __ldg(H1 + c * G + gi)) + c5 * __ldg(H2 + c * G + gi);
+        R_ hh = (c23 * h[c] - c16 * hp1[c]) + c5 * hp2[c];
         w[c] = R_(A.half_dt) * hh;
         HO[c * G + gi] = h[c];
       }
@@ -298,8 +322,7 @@ __global__ void __launch_bounds__(32 * kWarps) dns_kernel(Args A) {
           float lo = u.lo[c] + e;
           float hi = s + lo;
           lo = lo - (hi - s);
-          A.ff_out[c * G + gi] = hi;
-          A.ff_out[(3 + c) * G + gi] = lo;
+          A.ff_out[c * G + gi] = make_float2(hi, lo);
           bad |= !isfinite(hi);
         }
       } else {
