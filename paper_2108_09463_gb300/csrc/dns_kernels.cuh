@@ -133,6 +133,18 @@ __device__ __forceinline__ Node<FF> load_node(const Args& A, long long idx) {
   return r;
 }
 
+// Asynchronous global -> shared copies (cp.async, cached in L1 and L2) and
+// their group bookkeeping. Each lane copies and later reads only its own
+// elements, so the group waits are the only synchronisation needed.
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   float bb = s - a;
@@ -219,19 +231,60 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   }
   // q in [r0 - R, r1 + R) and n0 >= 4 > R: one add or subtract wraps it
   auto wrap = [&](int q) { return q < 0 ? q + n0 : (q >= n0 ? q - n0 : q); };
-  auto load_row = [&](int q) {
-    const int row = TWO_D ? wrap(q) : 0;
-    return load_node<FF>(A, (long long)row * n1 + xl);
+  // Rows arrive through a per-warp ring of DEPTH shared-memory slots filled by
+  // cp.async, DEPTH - 1 rows ahead of the row being consumed; the slot of state
+  // row q also receives the history of the row it completes, q - R (MPEA).
+  constexpr int DEPTH = 3;
+  constexpr int HD = (MODE == kField) ? 1 : DEPTH;
+  __shared__ unsigned long long s_st[TWO_D ? kWarps : 1][TWO_D ? DEPTH : 1][3][32];   // float2 or double
+  __shared__ R_ s_h[TWO_D ? kWarps : 1][TWO_D ? HD : 1][2][3][32];
+  const int q_first = r0 - RR, q_last = TWO_D ? r1 - 1 + RR : 0;
+  auto slot_of = [&](int q) { return (q - q_first) % DEPTH; };
+  auto issue = [&](int q) {
+    if (q <= q_last) {
+      const int sl = slot_of(q);
+      const long long idx = (long long)wrap(q) * n1 + xl;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (FF) cp_async(&s_st[wib][sl][c][lane], A.ff + c * A.G + idx, 8);
+        else cp_async(&s_st[wib][sl][c][lane], A.m64 + c * A.G + idx, 8);
+      }
+      if constexpr (MODE != kField) {
+        const int pr = q - RR;
+        if (pr >= r0 && pr < r1) {
+          const long long gi = (long long)pr * n1 + xl;
+          const R_* H1 = reinterpret_cast<const R_*>(A.h1);
+          const R_* H2 = reinterpret_cast<const R_*>(A.h2);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            cp_async(&s_h[wib][sl % HD][0][c][lane], H1 + c * A.G + gi, (int)sizeof(R_));
+            cp_async(&s_h[wib][sl % HD][1][c][lane], H2 + c * A.G + gi, (int)sizeof(R_));
+          }
+        }
+      }
+    }
+    cp_async_commit();      // one group per row, empty past the last row
   };
-  // the window takes row q, which `nxt` holds; the load of row q + 1 is issued
-  // at once (when q + 1 <= q_last) so that it is in flight during row q's work
-  const int q_last = TWO_D ? r1 - 1 + RR : 0;
-  Node<FF> nxt = load_row(TWO_D ? r0 - RR : 0);
   auto push_row = [&](int q) {
 #pragma unroll
     for (int k = 0; k < RR; ++k) win[k] = win[k + 1];
-    win[RR] = nxt;
-    if (q < q_last) nxt = load_row(q + 1);
+    if constexpr (TWO_D) {
+      cp_async_wait<DEPTH - 2>();                    // row q's group is complete
+      const int sl = slot_of(q);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (FF) {
+          const float2 v = *reinterpret_cast<const float2*>(&s_st[wib][sl][c][lane]);
+          win[RR].hi[c] = v.x;
+          win[RR].lo[c] = v.y;
+        } else {
+          win[RR].v[c] = *reinterpret_cast<const double*>(&s_st[wib][sl][c][lane]);
+        }
+      }
+      issue(q + DEPTH - 1);                          // into the slot row q - 1 used
+    } else {
+      win[RR] = load_node<FF>(A, xl);
+    }
   };
   // y-face flux from the full window: order 4 the face between rows q-2 and q-1
   // (rows q-3..q), order 2 the face between rows q-1 and q
@@ -254,14 +307,23 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   auto emit = [&](int p, const Node<FF>& u) {
     const long long gi = (long long)p * n1 + xl;
     const long long G = A.G;
-    R_ hp1[3], hp2[3];                               // h^{j-1}, h^{j-2}: loads issued first
+    R_ hp1[3], hp2[3];                               // h^{j-1}, h^{j-2}
     if constexpr (MODE != kField) {
-      const R_* H1 = reinterpret_cast<const R_*>(A.h1);
-      const R_* H2 = reinterpret_cast<const R_*>(A.h2);
+      if constexpr (TWO_D) {
+        const int sl = slot_of(p + RR) % HD;          // arrived with state row p + R
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        hp1[c] = out_lane ? __ldg(H1 + c * G + gi) : R_(0);
-        hp2[c] = out_lane ? __ldg(H2 + c * G + gi) : R_(0);
+        for (int c = 0; c < 3; ++c) {
+          hp1[c] = s_h[wib][sl][0][c][lane];
+          hp2[c] = s_h[wib][sl][1][c][lane];
+        }
+      } else {
+        const R_* H1 = reinterpret_cast<const R_*>(A.h1);
+        const R_* H2 = reinterpret_cast<const R_*>(A.h2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          hp1[c] = out_lane ? __ldg(H1 + c * G + gi) : R_(0);
+          hp2[c] = out_lane ? __ldg(H2 + c * G + gi) : R_(0);
+        }
       }
     }
     R_ ax;
@@ -340,9 +402,12 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   if constexpr (!TWO_D) {
     push_row(0);
     emit(0, win[RR]);
+    (void)q_first;
   } else {
     // rows r0-R..r0-1 fill the window; rows r0..r0+R-1 also push their faces;
     // from row r0+R on each new row completes row p = q - R (p in [r0, r1))
+#pragma unroll
+    for (int k = 0; k < DEPTH - 1; ++k) issue(q_first + k);
     for (int q = r0 - RR; q < r0; ++q) push_row(q);
     for (int q = r0; q < r0 + RR; ++q) {
       push_row(q);
