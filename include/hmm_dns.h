@@ -61,10 +61,11 @@ typedef struct {
   int reserved[4];              /* must be zero                                    */
 } hmm_dns_params;
 
-/* Validates the parameters (including a > 0 at every face, (A1)), tabulates the
- * coefficient's per-axis factors, picks the time step and allocates the state:
- * 2 state buffers and 3 history buffers of G points (FP64: 24 B per point each;
- * FP32 form: 24 B state, 12 B history) plus 4 FP64 start-up buffers.
+/* Validates the parameters (including a > 0 at every face, (A1)), tabulates
+ * a^eps at every face (d x G values, FP64 and FP32 copies), picks the time step
+ * and allocates the state: 2 state buffers and 3 history buffers of G points
+ * (FP64: 24 B per point each; FP32 form: 24 B state, 12 B history) plus 4 FP64
+ * start-up buffers.
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream). */
 hmm_status hmm_dns_init(const hmm_dns_params* params, void* cuda_stream, void** handle_out);
 

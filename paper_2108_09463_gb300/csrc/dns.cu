@@ -26,6 +26,7 @@ using namespace hmm_dns;
 namespace {
 
 thread_local std::string g_dns_init_error;
+constexpr int kMaxTerms = 8;   // coefficient terms accepted (as in hmm_params)
 
 struct DnsHandle {
   hmm_dns_params p{};
@@ -37,12 +38,9 @@ struct DnsHandle {
   double dt = 0, a_max = 0;
   long long j = 0;
   int cur = 0;                    // state buffer holding the current state
-  bool tab = false;               // face table in use
   Args base{};
   // device memory
-  double* d_tab64 = nullptr;      // tfx | tnx | tfy | tny
-  float* d_tab32 = nullptr;
-  double* d_face64 = nullptr;     // ax | ay (G each)
+  double* d_face64 = nullptr;     // ax | ay (G each): faces along the fast, the slow axis
   float* d_face32 = nullptr;
   void* d_state[2] = {nullptr, nullptr};   // FP64: 3G doubles; FF: 6G floats
   void* d_hist[3] = {nullptr, nullptr, nullptr};
@@ -200,37 +198,33 @@ __global__ void dns_join(long long G, const float2* S, double* M) {
 int pw_blocks(long long G) { return (int)((G + 255) / 256); }
 
 // ------------------------------------------------------------ stencil launch
-template <int ORDER, bool TWO_D, bool TAB>
+template <int ORDER, bool TWO_D>
 cudaError_t launch_mode(int mode, const Args& a, cudaStream_t st) {
   const int blocks = (a.items + kWarps - 1) / kWarps;
-  if (mode == kField) dns_kernel<ORDER, TWO_D, TAB, kField><<<blocks, 32 * kWarps, 0, st>>>(a);
-  else if (mode == kMpea64) dns_kernel<ORDER, TWO_D, TAB, kMpea64><<<blocks, 32 * kWarps, 0, st>>>(a);
-  else dns_kernel<ORDER, TWO_D, TAB, kMpeaFF><<<blocks, 32 * kWarps, 0, st>>>(a);
+  if (mode == kField) dns_kernel<ORDER, TWO_D, kField><<<blocks, 32 * kWarps, 0, st>>>(a);
+  else if (mode == kMpea64) dns_kernel<ORDER, TWO_D, kMpea64><<<blocks, 32 * kWarps, 0, st>>>(a);
+  else dns_kernel<ORDER, TWO_D, kMpeaFF><<<blocks, 32 * kWarps, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stencil(int mode, const DnsHandle* h, const Args& a) {
   const bool two = h->d == 2;
-  if (h->order == 4) {
-    if (two) return h->tab ? launch_mode<4, true, true>(mode, a, h->stream) : launch_mode<4, true, false>(mode, a, h->stream);
-    return h->tab ? launch_mode<4, false, true>(mode, a, h->stream) : launch_mode<4, false, false>(mode, a, h->stream);
-  }
-  if (two) return h->tab ? launch_mode<2, true, true>(mode, a, h->stream) : launch_mode<2, true, false>(mode, a, h->stream);
-  return h->tab ? launch_mode<2, false, true>(mode, a, h->stream) : launch_mode<2, false, false>(mode, a, h->stream);
+  if (h->order == 4) return two ? launch_mode<4, true>(mode, a, h->stream) : launch_mode<4, false>(mode, a, h->stream);
+  return two ? launch_mode<2, true>(mode, a, h->stream) : launch_mode<2, false>(mode, a, h->stream);
 }
 
 // Resident warps of the time-stepping kernel on the whole GPU (occupancy of
 // its instantiation times the SM count); 152 * 16 if the device cannot be asked.
-template <int ORDER, bool TWO_D, bool TAB>
+template <int ORDER, bool TWO_D>
 long long resident_warps_of(int mode) {
   int dev = 0, sms = 0, blocks = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
     if (mode == kMpeaFF)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dns_kernel<ORDER, TWO_D, TAB, kMpeaFF>, 32 * kWarps, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dns_kernel<ORDER, TWO_D, kMpeaFF>, 32 * kWarps, 0);
     else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dns_kernel<ORDER, TWO_D, TAB, kMpea64>, 32 * kWarps, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dns_kernel<ORDER, TWO_D, kMpea64>, 32 * kWarps, 0);
   }
   if (e != cudaSuccess || sms <= 0 || blocks <= 0) {
     cudaGetLastError();
@@ -255,9 +249,7 @@ void plan_work(DnsHandle* h) {
     a.chunks = 1;
   } else {
     const int mode = h->precision == HMM_FP64_PLAIN ? kMpea64 : kMpeaFF;
-    long long target;
-    if (h->order == 4) target = h->tab ? resident_warps_of<4, true, true>(mode) : resident_warps_of<4, true, false>(mode);
-    else target = h->tab ? resident_warps_of<2, true, true>(mode) : resident_warps_of<2, true, false>(mode);
+    const long long target = h->order == 4 ? resident_warps_of<4, true>(mode) : resident_warps_of<2, true>(mode);
     long long ch = ((long long)h->n0 * a.strips + target - 1) / target;
     ch = std::max<long long>(8, std::min<long long>(ch, h->n0));
     a.chunk = (int)ch;
@@ -267,60 +259,62 @@ void plan_work(DnsHandle* h) {
 }
 
 // ------------------------------------------------------------ tables
-hmm_status upload_tables(DnsHandle* h) {
+// Copies face coefficients (fast-axis faces, then slow-axis faces; G each) to
+// the device in FP64 and FP32.
+hmm_status upload_faces(DnsHandle* h, const std::vector<double>& f64) {
+  std::vector<float> f32(f64.size());
+  for (size_t i = 0; i < f64.size(); ++i) f32[i] = (float)f64[i];
+  if (!h->d_face64) {
+    DNS_CUDA(h, cudaMalloc(&h->d_face64, f64.size() * sizeof(double)));
+    DNS_CUDA(h, cudaMalloc(&h->d_face32, f32.size() * sizeof(float)));
+  }
+  DNS_CUDA(h, cudaMemcpy(h->d_face64, f64.data(), f64.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DNS_CUDA(h, cudaMemcpy(h->d_face32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  Args& a = h->base;
+  a.ax64 = h->d_face64;
+  a.ay64 = h->d_face64 + h->G;
+  a.ax32 = h->d_face32;
+  a.ay32 = h->d_face32 + h->G;
+  return HMM_OK;
+}
+
+// a^eps at every face from the separable terms: per axis the terms' factors
+// are tabulated once (amp folded into the fast axis), then a_x(r, i) =
+// c0 + sum_t X_t(face i) Y_t(node r) and a_y(r, i) = c0 + sum_t X_t(node i) Y_t(face r).
+hmm_status build_faces(DnsHandle* h) {
   const int n0 = h->n0, n1 = h->n1, nt = (int)h->terms.size();
   const int kf = h->d - 1;               // axis index of the fast axis
-  std::vector<double> t64((size_t)2 * kMaxTerms * n1 + (size_t)2 * kMaxTerms * n0, 0.0);
-  double* tfx = t64.data();
-  double* tnx = tfx + (size_t)kMaxTerms * n1;
-  double* tfy = tnx + (size_t)kMaxTerms * n1;
-  double* tny = tfy + (size_t)kMaxTerms * n0;
+  std::vector<double> tfx((size_t)nt * n1), tnx((size_t)nt * n1), tfy((size_t)nt * n0, 1.0), tny((size_t)nt * n0, 1.0);
   for (int t = 0; t < nt; ++t) {
     const hmm_coef_term& T = h->terms[t];
     for (int i = 0; i < n1; ++i) {
       tfx[(size_t)t * n1 + i] = T.amp * term_factor(T, kf, (i + 0.5) * h->dx[1], h->p.eps);
       tnx[(size_t)t * n1 + i] = T.amp * term_factor(T, kf, i * h->dx[1], h->p.eps);
     }
-    for (int r = 0; r < n0; ++r) {
-      if (h->d == 2) {
-        tfy[(size_t)r * kMaxTerms + t] = term_factor(T, 0, (r + 0.5) * h->dx[0], h->p.eps);
-        tny[(size_t)r * kMaxTerms + t] = term_factor(T, 0, r * h->dx[0], h->p.eps);
-      } else {
-        tfy[(size_t)r * kMaxTerms + t] = 1.0;
-        tny[(size_t)r * kMaxTerms + t] = 1.0;
+    if (h->d == 2)
+      for (int r = 0; r < n0; ++r) {
+        tfy[(size_t)t * n0 + r] = term_factor(T, 0, (r + 0.5) * h->dx[0], h->p.eps);
+        tny[(size_t)t * n0 + r] = term_factor(T, 0, r * h->dx[0], h->p.eps);
       }
-    }
   }
-  // a > 0 at every face (A1): a_x(r, i) = c0 + sum_t tfx[t][i] tny[r][t], a_y(r, i) = c0 + sum_t tnx[t][i] tfy[r][t]
+  const long long G = h->G;
+  std::vector<double> f64((size_t)2 * G, 1.0);
   double amin = 1e300;
   for (int r = 0; r < n0; ++r)
     for (int i = 0; i < n1; ++i) {
       double ax = h->p.c0, ay = h->p.c0;
       for (int t = 0; t < nt; ++t) {
-        ax += tfx[(size_t)t * n1 + i] * tny[(size_t)r * kMaxTerms + t];
-        ay += tnx[(size_t)t * n1 + i] * tfy[(size_t)r * kMaxTerms + t];
+        ax += tfx[(size_t)t * n1 + i] * tny[(size_t)t * n0 + r];
+        ay += tnx[(size_t)t * n1 + i] * tfy[(size_t)t * n0 + r];
       }
+      const long long g = (long long)r * n1 + i;
+      f64[g] = ax;
+      if (h->d == 2) f64[G + g] = ay;
       amin = std::min(amin, h->d == 2 ? std::min(ax, ay) : ax);
     }
+  // a > 0 at every face (A1)
   if (!(amin > 0)) return fail(h, HMM_ERR_INVALID_ARG, "coefficient a^eps <= 0 at a face (A1)");
-  std::vector<float> t32(t64.size());
-  for (size_t i = 0; i < t64.size(); ++i) t32[i] = (float)t64[i];
-  DNS_CUDA(h, cudaMalloc(&h->d_tab64, t64.size() * sizeof(double)));
-  DNS_CUDA(h, cudaMalloc(&h->d_tab32, t32.size() * sizeof(float)));
-  DNS_CUDA(h, cudaMemcpy(h->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
-  DNS_CUDA(h, cudaMemcpy(h->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
-  Args& a = h->base;
-  a.nt = nt;
-  a.c0 = h->p.c0;
-  a.tfx = h->d_tab64;
-  a.tnx = a.tfx + (size_t)kMaxTerms * n1;
-  a.tfy = a.tnx + (size_t)kMaxTerms * n1;
-  a.tny = a.tfy + (size_t)kMaxTerms * n0;
-  a.sfx = h->d_tab32;
-  a.snx = a.sfx + (size_t)kMaxTerms * n1;
-  a.sfy = a.snx + (size_t)kMaxTerms * n1;
-  a.sny = a.sfy + (size_t)kMaxTerms * n0;
-  return HMM_OK;
+  return upload_faces(h, f64);
 }
 
 hmm_status pick_dt(DnsHandle* h) {
@@ -344,7 +338,7 @@ hmm_status pick_dt(DnsHandle* h) {
 }
 
 void free_all(DnsHandle* h) {
-  void* ptrs[] = {h->d_tab64, h->d_tab32, h->d_face64, h->d_face32, h->d_state[0], h->d_state[1],
+  void* ptrs[] = {h->d_face64, h->d_face32, h->d_state[0], h->d_state[1],
                   h->d_hist[0], h->d_hist[1], h->d_hist[2], h->d_m64, h->d_stage, h->d_H, h->d_acc,
                   h->d_host_io, h->d_err};
   for (void* p : ptrs)
@@ -509,7 +503,7 @@ hmm_status hmm_dns_init(const hmm_dns_params* params, void* cuda_stream, void** 
   };
   if (!(h->a_max > 0)) { h->err = "coefficient upper bound must be positive"; return bail(HMM_ERR_INVALID_ARG); }
   plan_work(h);
-  hmm_status s = upload_tables(h);
+  hmm_status s = build_faces(h);
   if (s != HMM_OK) return bail(s);
   s = pick_dt(h);
   if (s != HMM_OK) return bail(s);
@@ -555,20 +549,7 @@ hmm_status hmm_dns_set_face_table(void* handle, const double* table_host, long l
   } else {
     std::copy(table_host, table_host + G, f64.begin());
   }
-  std::vector<float> f32(f64.size());
-  for (size_t i = 0; i < f64.size(); ++i) f32[i] = (float)f64[i];
-  if (!h->d_face64) {
-    DNS_CUDA(h, cudaMalloc(&h->d_face64, f64.size() * sizeof(double)));
-    DNS_CUDA(h, cudaMalloc(&h->d_face32, f32.size() * sizeof(float)));
-  }
-  DNS_CUDA(h, cudaMemcpy(h->d_face64, f64.data(), f64.size() * sizeof(double), cudaMemcpyHostToDevice));
-  DNS_CUDA(h, cudaMemcpy(h->d_face32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice));
-  h->base.ax64 = h->d_face64;
-  h->base.ay64 = h->d_face64 + G;
-  h->base.ax32 = h->d_face32;
-  h->base.ay32 = h->d_face32 + G;
-  h->tab = true;
-  plan_work(h);
+  DNS_TRY(upload_faces(h, f64));
   h->a_max = amax;
   DNS_TRY(pick_dt(h));
   h->j = 0;

@@ -7,24 +7,25 @@
 // wrap). Along the fast axis the staggered differences take their neighbours
 // from the other lanes by warp shuffles; along the slow axis each lane keeps
 // its own column's last R+1 rows and the last R+1 face fluxes in registers, so
-// a node's y-divergence is complete R rows after it was loaded. Nothing goes
-// through shared memory and no barrier wider than the warp is needed. Every
-// node is read once per chunk (plus 2R halo rows per chunk and the 2R halo
-// lanes per strip, which the L2 serves).
+// a node's y-divergence is complete R rows after it was loaded. No barrier
+// wider than the warp is needed.
+//
+// Rows arrive through a per-warp ring of shared-memory slots that cp.async
+// fills two rows ahead of the row being consumed: the state row, the two face
+// coefficients that row brings into use, and (time stepping) the history of
+// the row it completes. Each lane copies and reads only its own elements.
 //
 // Face fluxes F_f = a_f * G_f with the raw differences
 //   order 4: G_f = (u_{f-1} - u_{f+2}) + 27 (u_{f+1} - u_f),   H += c ((F_{x-2} - F_{x+1}) + 27 (F_x - F_{x-1}))
 //   order 2: G_f = u_{f+1} - u_f,                               H += c (F_x - F_{x-1})
-// (face f between nodes f and f+1), c = 1/(24 dx)^2 or 1/dx^2 per axis.
+// (face f between nodes f and f+1), c = 1/(24 dx)^2 or 1/dx^2 per axis. The
+// coefficient a^eps at the faces is a table of G values per axis (built by the
+// host from the separable terms, or given by the caller).
 //
-// In the float-float form (FF) a node is (hi, lo) per component, stored as one
-// float2 per component; each difference is taken on hi and on lo separately
-// and summed, so that it keeps FP32 accuracy relative to its own size instead
-// of to |m|.
-//
-// Latency hiding: the next row's loads and the output row's history loads are
-// issued before the current row's arithmetic, and the per-lane coefficient
-// factors live in shared memory instead of registers.
+// In the float-float form (FF) a node is (hi, lo) per component, one float2;
+// each difference is taken on hi and lo together with packed FP32x2
+// arithmetic and then summed, so that it keeps FP32 accuracy relative to its
+// own size instead of to |m|.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,7 +34,6 @@
 
 namespace hmm_dns {
 
-constexpr int kMaxTerms = 8;
 constexpr int kWarps = 4;           // warps per block (one work item each)
 constexpr int kErrNonFinite = 1;
 
@@ -44,13 +44,8 @@ struct Args {
   long long G;           // n0 * n1
   int strips, chunk, chunks, items;
   double cx, cy;         // stencil scale along the fast and the slow axis
-  int nt;                // separable terms (0 with a face table)
-  double c0;
-  // separable tables: fast axis [nt][n1] (faces with amp folded in, nodes with
-  // amp folded in), slow axis [n0][kMaxTerms] (faces, nodes), FP64 and FP32
-  const double* tfx; const double* tnx; const double* tfy; const double* tny;
-  const float* sfx; const float* snx; const float* sfy; const float* sny;
-  // face tables (TAB): faces along the fast axis and along the slow axis, G each
+  // face coefficients: faces along the fast axis (between x and x+1) and along
+  // the slow axis (between rows y and y+1), G each, FP64 and FP32 copies
   const double* ax64; const double* ay64;
   const float* ax32; const float* ay32;
   double alpha, half_dt;
@@ -64,38 +59,32 @@ struct Args {
 
 template <bool FF> struct Node;
 template <> struct Node<false> { double v[3]; };
-template <> struct Node<true> { float hi[3]; float lo[3]; };
+template <> struct Node<true> { float2 v[3]; };       // (hi, lo)
 
 template <typename T>
 __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 template <typename T>
 __device__ __forceinline__ T shfl_dn(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ float2 shfl_up(float2 v, int d) { return make_float2(shfl_up(v.x, d), shfl_up(v.y, d)); }
+__device__ __forceinline__ float2 shfl_dn(float2 v, int d) { return make_float2(shfl_dn(v.x, d), shfl_dn(v.y, d)); }
 
 template <bool FF>
 __device__ __forceinline__ Node<FF> node_shfl_up(const Node<FF>& a, int d) {
   Node<FF> r;
-  if constexpr (FF) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { r.hi[c] = shfl_up(a.hi[c], d); r.lo[c] = shfl_up(a.lo[c], d); }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) r.v[c] = shfl_up(a.v[c], d);
-  }
+  for (int c = 0; c < 3; ++c) r.v[c] = shfl_up(a.v[c], d);
   return r;
 }
 
 template <bool FF>
 __device__ __forceinline__ Node<FF> node_shfl_dn(const Node<FF>& a, int d) {
   Node<FF> r;
-  if constexpr (FF) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { r.hi[c] = shfl_dn(a.hi[c], d); r.lo[c] = shfl_dn(a.lo[c], d); }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) r.v[c] = shfl_dn(a.v[c], d);
-  }
+  for (int c = 0; c < 3; ++c) r.v[c] = shfl_dn(a.v[c], d);
   return r;
 }
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 // Raw face difference of component c: order 4 from (u_{f-1}, u_f, u_{f+1}, u_{f+2}),
 // order 2 from (u_f, u_{f+1}) passed as (b, c1).
@@ -104,11 +93,11 @@ __device__ __forceinline__ auto face_diff(const Node<FF>& a, const Node<FF>& b, 
                                           const Node<FF>& d, int c) {
   if constexpr (FF) {
     if constexpr (ORDER == 4) {
-      float gh = (a.hi[c] - d.hi[c]) + 27.0f * (c1.hi[c] - b.hi[c]);
-      float gl = (a.lo[c] - d.lo[c]) + 27.0f * (c1.lo[c] - b.lo[c]);
-      return gh + gl;
+      const float2 g = __ffma2_rn(make_float2(27.f, 27.f), sub2(c1.v[c], b.v[c]), sub2(a.v[c], d.v[c]));
+      return g.x + g.y;
     } else {
-      return (c1.hi[c] - b.hi[c]) + (c1.lo[c] - b.lo[c]);
+      const float2 g = sub2(c1.v[c], b.v[c]);
+      return g.x + g.y;
     }
   } else {
     if constexpr (ORDER == 4) return (a.v[c] - d.v[c]) + 27.0 * (c1.v[c] - b.v[c]);
@@ -119,16 +108,10 @@ __device__ __forceinline__ auto face_diff(const Node<FF>& a, const Node<FF>& b, 
 template <bool FF>
 __device__ __forceinline__ Node<FF> load_node(const Args& A, long long idx) {
   Node<FF> r;
-  if constexpr (FF) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float2 v = __ldg(A.ff + c * A.G + idx);
-      r.hi[c] = v.x;
-      r.lo[c] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) r.v[c] = __ldg(A.m64 + c * A.G + idx);
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (FF) r.v[c] = __ldg(A.ff + c * A.G + idx);
+    else r.v[c] = __ldg(A.m64 + c * A.G + idx);
   }
   return r;
 }
@@ -151,8 +134,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// x-part of H at the lane's node (raw, unscaled) from the row's nodes `u`.
-// Returns the divergence of the face fluxes; valid on lanes R..31-R.
+// x-part of H at the lane's node (raw, unscaled) from the row's nodes `u`,
+// the divergence of the face fluxes; valid on lanes R..31-R.
 template <int ORDER, bool FF, typename R_>
 __device__ __forceinline__ void x_part(const Node<FF>& u, R_ ax, R_ out[3]) {
   Node<FF> um1, up1, up2;
@@ -176,14 +159,13 @@ __device__ __forceinline__ void x_part(const Node<FF>& u, R_ ax, R_ out[3]) {
   }
 }
 
-template <int ORDER, bool TWO_D, bool TAB, int MODE>
+template <int ORDER, bool TWO_D, int MODE>
 __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_kernel(Args A) {
   constexpr bool FF = (MODE == kMpeaFF);
   using R_ = typename std::conditional<FF, float, double>::type;
+  using S_ = typename std::conditional<FF, float2, double>::type;   // state element
   constexpr int RR = (ORDER == 4) ? 3 : 1;
   constexpr int W = 32 - 2 * RR;
-  // per-lane separable factors of the fast axis (amp folded in): faces, nodes
-  __shared__ R_ s_fac[kWarps][2][kMaxTerms][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int item = blockIdx.x * kWarps + wib;
   if (item >= A.items) return;                      // whole warp leaves together
@@ -195,26 +177,9 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   xl = (xl % n1 + n1) % n1;
   const int r0 = TWO_D ? chunk * A.chunk : 0;
   const int r1 = TWO_D ? min(r0 + A.chunk, n0) : 1;
-  const int nt = A.nt;
-  if constexpr (!TAB) {
-    for (int t = 0; t < nt; ++t) {
-      if constexpr (FF) {
-        s_fac[wib][0][t][lane] = __ldg(A.sfx + t * n1 + xl);
-        s_fac[wib][1][t][lane] = __ldg(A.snx + t * n1 + xl);
-      } else {
-        s_fac[wib][0][t][lane] = __ldg(A.tfx + t * n1 + xl);
-        s_fac[wib][1][t][lane] = __ldg(A.tnx + t * n1 + xl);
-      }
-    }
-    __syncwarp();
-  }
-  // c0 + sum_t fac_t(lane) * rowtab[row][t] (which = 0: fast-axis faces, 1: nodes)
-  auto coef = [&](int which, const void* rowtab, int row) -> R_ {
-    const R_* rt = reinterpret_cast<const R_*>(rowtab) + (long long)row * kMaxTerms;
-    R_ a = R_(A.c0);
-    for (int t = 0; t < nt; ++t) a += s_fac[wib][which][t][lane] * __ldg(rt + t);
-    return a;
-  };
+  const S_* state = FF ? reinterpret_cast<const S_*>(A.ff) : reinterpret_cast<const S_*>(A.m64);
+  const R_* AX = FF ? reinterpret_cast<const R_*>(A.ax32) : reinterpret_cast<const R_*>(A.ax64);
+  const R_* AY = FF ? reinterpret_cast<const R_*>(A.ay32) : reinterpret_cast<const R_*>(A.ay64);
 
   // Rolling state of the own column: rows q-R..q and the last R+1 y-face fluxes
   // (order 4: faces q-5..q-2, order 2: faces q-2..q-1), oldest first.
@@ -225,34 +190,36 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       fq[k][c] = R_(0);
-      if constexpr (FF) { win[k].hi[c] = 0.f; win[k].lo[c] = 0.f; }
+      if constexpr (FF) win[k].v[c] = make_float2(0.f, 0.f);
       else win[k].v[c] = 0.0;
     }
   }
   // q in [r0 - R, r1 + R) and n0 >= 4 > R: one add or subtract wraps it
   auto wrap = [&](int q) { return q < 0 ? q + n0 : (q >= n0 ? q - n0 : q); };
-  // Rows arrive through a per-warp ring of DEPTH shared-memory slots filled by
-  // cp.async, DEPTH - 1 rows ahead of the row being consumed; the slot of state
-  // row q also receives the history of the row it completes, q - R (MPEA).
+  // The ring: DEPTH slots per warp; the slot of state row q also holds a_y of
+  // the face row q brings into use (q-2 for order 4, q-1 for order 2), and a_x
+  // and the history of the row q completes, q - R, when that row is an output.
   constexpr int DEPTH = 3;
   constexpr int HD = (MODE == kField) ? 1 : DEPTH;
-  __shared__ unsigned long long s_st[TWO_D ? kWarps : 1][TWO_D ? DEPTH : 1][3][32];   // float2 or double
-  __shared__ R_ s_h[TWO_D ? kWarps : 1][TWO_D ? HD : 1][2][3][32];
+  constexpr int WK = TWO_D ? kWarps : 1;
+  __shared__ S_ s_st[WK][TWO_D ? DEPTH : 1][3][32];
+  __shared__ R_ s_a[WK][TWO_D ? DEPTH : 1][2][32];
+  __shared__ R_ s_h[WK][TWO_D ? HD : 1][2][3][32];
   const int q_first = r0 - RR, q_last = TWO_D ? r1 - 1 + RR : 0;
   auto slot_of = [&](int q) { return (q - q_first) % DEPTH; };
+  auto face_row = [&](int q) { return wrap(ORDER == 4 ? q - 2 : q - 1); };
   auto issue = [&](int q) {
     if (q <= q_last) {
       const int sl = slot_of(q);
       const long long idx = (long long)wrap(q) * n1 + xl;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if constexpr (FF) cp_async(&s_st[wib][sl][c][lane], A.ff + c * A.G + idx, 8);
-        else cp_async(&s_st[wib][sl][c][lane], A.m64 + c * A.G + idx, 8);
-      }
-      if constexpr (MODE != kField) {
-        const int pr = q - RR;
-        if (pr >= r0 && pr < r1) {
-          const long long gi = (long long)pr * n1 + xl;
+      for (int c = 0; c < 3; ++c) cp_async(&s_st[wib][sl][c][lane], state + c * A.G + idx, 8);
+      if (q >= r0) cp_async(&s_a[wib][sl][1][lane], AY + (long long)face_row(q) * n1 + xl, (int)sizeof(R_));
+      const int pr = q - RR;
+      if (pr >= r0 && pr < r1) {
+        const long long gi = (long long)pr * n1 + xl;
+        cp_async(&s_a[wib][sl][0][lane], AX + gi, (int)sizeof(R_));
+        if constexpr (MODE != kField) {
           const R_* H1 = reinterpret_cast<const R_*>(A.h1);
           const R_* H2 = reinterpret_cast<const R_*>(A.h2);
 #pragma unroll
@@ -272,15 +239,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
       cp_async_wait<DEPTH - 2>();                    // row q's group is complete
       const int sl = slot_of(q);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if constexpr (FF) {
-          const float2 v = *reinterpret_cast<const float2*>(&s_st[wib][sl][c][lane]);
-          win[RR].hi[c] = v.x;
-          win[RR].lo[c] = v.y;
-        } else {
-          win[RR].v[c] = *reinterpret_cast<const double*>(&s_st[wib][sl][c][lane]);
-        }
-      }
+      for (int c = 0; c < 3; ++c) win[RR].v[c] = s_st[wib][sl][c][lane];
       issue(q + DEPTH - 1);                          // into the slot row q - 1 used
     } else {
       win[RR] = load_node<FF>(A, xl);
@@ -289,10 +248,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   // y-face flux from the full window: order 4 the face between rows q-2 and q-1
   // (rows q-3..q), order 2 the face between rows q-1 and q
   auto push_face = [&](int q) {
-    const int frow = wrap(ORDER == 4 ? q - 2 : q - 1);
-    R_ ay;
-    if constexpr (TAB) ay = FF ? R_(__ldg(A.ay32 + (long long)frow * n1 + xl)) : R_(__ldg(A.ay64 + (long long)frow * n1 + xl));
-    else ay = coef(1, FF ? (const void*)A.sfy : (const void*)A.tfy, frow);
+    const R_ ay = s_a[wib][slot_of(q)][1][lane];
 #pragma unroll
     for (int k = 0; k < RR; ++k)
 #pragma unroll
@@ -307,28 +263,29 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   auto emit = [&](int p, const Node<FF>& u) {
     const long long gi = (long long)p * n1 + xl;
     const long long G = A.G;
-    R_ hp1[3], hp2[3];                               // h^{j-1}, h^{j-2}
-    if constexpr (MODE != kField) {
-      if constexpr (TWO_D) {
-        const int sl = slot_of(p + RR) % HD;          // arrived with state row p + R
+    R_ ax, hp1[3], hp2[3];                           // a_x, h^{j-1}, h^{j-2}
+    if constexpr (TWO_D) {
+      const int sl = slot_of(p + RR);                // arrived with state row p + R
+      ax = s_a[wib][sl][0][lane];
+      if constexpr (MODE != kField) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          hp1[c] = s_h[wib][sl][0][c][lane];
-          hp2[c] = s_h[wib][sl][1][c][lane];
+          hp1[c] = s_h[wib][sl % HD][0][c][lane];
+          hp2[c] = s_h[wib][sl % HD][1][c][lane];
         }
-      } else {
+      }
+    } else {
+      ax = __ldg(AX + gi);
+      if constexpr (MODE != kField) {
         const R_* H1 = reinterpret_cast<const R_*>(A.h1);
         const R_* H2 = reinterpret_cast<const R_*>(A.h2);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          hp1[c] = out_lane ? __ldg(H1 + c * G + gi) : R_(0);
-          hp2[c] = out_lane ? __ldg(H2 + c * G + gi) : R_(0);
+          hp1[c] = __ldg(H1 + c * G + gi);
+          hp2[c] = __ldg(H2 + c * G + gi);
         }
       }
     }
-    R_ ax;
-    if constexpr (TAB) ax = FF ? R_(__ldg(A.ax32 + (long long)p * n1 + xl)) : R_(__ldg(A.ax64 + (long long)p * n1 + xl));
-    else ax = coef(0, FF ? (const void*)A.sny : (const void*)A.tny, p);
     R_ H[3];
     x_part<ORDER, FF, R_>(u, ax, H);
 #pragma unroll
@@ -348,7 +305,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
       R_ m[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if constexpr (FF) m[c] = u.hi[c];
+        if constexpr (FF) m[c] = u.v[c].x;
         else m[c] = u.v[c];
       }
       const R_ al = R_(A.alpha);
@@ -380,8 +337,8 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           float s, e;
-          two_sum(u.hi[c], dl[c], s, e);
-          float lo = u.lo[c] + e;
+          two_sum(u.v[c].x, dl[c], s, e);
+          float lo = u.v[c].y + e;
           float hi = s + lo;
           lo = lo - (hi - s);
           A.ff_out[c * G + gi] = make_float2(hi, lo);
@@ -403,6 +360,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
     push_row(0);
     emit(0, win[RR]);
     (void)q_first;
+    (void)q_last;
   } else {
     // rows r0-R..r0-1 fill the window; rows r0..r0+R-1 also push their faces;
     // from row r0+R on each new row completes row p = q - R (p in [r0, r1))
