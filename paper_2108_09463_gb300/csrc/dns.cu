@@ -31,7 +31,10 @@ constexpr int kMaxTerms = 8;   // coefficient terms accepted (as in hmm_params)
 struct DnsHandle {
   hmm_dns_params p{};
   std::vector<hmm_coef_term> terms;
-  cudaStream_t stream = nullptr;
+  cudaStream_t user = nullptr;    // the caller's stream
+  cudaStream_t stream = nullptr;  // the library's own non-blocking stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph[2][3] = {};   // six MPEA steps, by (cur, j mod 3) at their start
   int d = 1, n0 = 1, n1 = 1, order = 4, precision = 0;
   long long G = 0;
   double dx[2] = {0, 0};          // slow, fast axis spacing
@@ -345,6 +348,20 @@ void free_all(DnsHandle* h) {
     if (p) cudaFree(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  for (auto& row : h->graph)
+    for (auto& g : row)
+      if (g) cudaGraphExecDestroy(g);
+  if (h->stream) cudaStreamDestroy(h->stream);
+}
+
+void drop_graphs(DnsHandle* h) {
+  for (auto& row : h->graph)
+    for (auto& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
 }
 
 DnsHandle* as_handle(void* p) { return reinterpret_cast<DnsHandle*>(p); }
@@ -392,11 +409,50 @@ hmm_status enqueue_mpea_step(DnsHandle* h) {
   return HMM_OK;
 }
 
+// Six MPEA steps (the state ping-pong and the three history slots both return
+// to where they started) as one CUDA graph, captured on first use for the
+// current (cur, j mod 3) and replayed afterwards.
+hmm_status launch_six(DnsHandle* h) {
+  cudaGraphExec_t& g = h->graph[h->cur][h->j % 3];
+  if (!g) {
+    const int cur0 = h->cur;
+    const long long j0 = h->j;
+    DNS_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    hmm_status st = HMM_OK;
+    for (int k = 0; k < 6 && st == HMM_OK; ++k) {
+      st = enqueue_mpea_step(h);
+      h->j += 1;
+    }
+    h->cur = cur0;
+    h->j = j0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st != HMM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g = nullptr;
+      return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+  }
+  DNS_CUDA(h, cudaGraphLaunch(g, h->stream));
+  h->j += 6;                      // cur is unchanged after an even number of steps
+  return HMM_OK;
+}
+
 // The current state lives in d_state[cur] (FP64 form always; FF form once the
-// start-up is over) or, during the FF form's start-up, in d_m64.
+// start-up is over) or, during the FF form's start-up, in d_m64. The work runs
+// on the library's stream, ordered after the caller's stream and before its
+// later work by events.
 hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
   const long long G = h->G;
   const size_t bytes64 = (size_t)3 * G * sizeof(double);
+  DNS_CUDA(h, cudaEventRecord(h->ev_in, h->user));
+  DNS_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0));
   DNS_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   DNS_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   const bool ff = h->precision != HMM_FP64_PLAIN;
@@ -409,17 +465,25 @@ hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
     DNS_CUDA(h, cudaMemcpyAsync(m64, M_dev, bytes64, cudaMemcpyDeviceToDevice, h->stream));
     if (!ff) in_m64 = false;    // FP64: d_state[cur] is m64
   }
-  for (int s = 0; s < n_steps; ++s) {
+  for (int s = 0; s < n_steps;) {
     if (h->j < 2) {
       DNS_TRY(enqueue_rk4_step(h, ff ? h->d_m64 : (double*)h->d_state[h->cur]));
-    } else {
-      if (ff && in_m64) {
-        dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, h->d_m64, (float2*)h->d_state[h->cur]);
-        in_m64 = false;
-      }
-      DNS_TRY(enqueue_mpea_step(h));
+      h->j += 1;
+      s += 1;
+      continue;
     }
-    h->j += 1;
+    if (ff && in_m64) {
+      dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, h->d_m64, (float2*)h->d_state[h->cur]);
+      in_m64 = false;
+    }
+    if (n_steps - s >= 6) {
+      DNS_TRY(launch_six(h));
+      s += 6;
+    } else {
+      DNS_TRY(enqueue_mpea_step(h));
+      h->j += 1;
+      s += 1;
+    }
   }
   if (ff && !in_m64) {
     dns_join<<<pw_blocks(G), 256, 0, h->stream>>>(G, (const float2*)h->d_state[h->cur], M_dev);
@@ -431,6 +495,8 @@ hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
   DNS_CUDA(h, cudaEventRecord(h->ev1, h->stream));
   int err = 0;
   DNS_CUDA(h, cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DNS_CUDA(h, cudaEventRecord(h->ev_out, h->stream));
+  DNS_CUDA(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
   DNS_CUDA(h, cudaStreamSynchronize(h->stream));
   float ms = 0;
   DNS_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -480,7 +546,7 @@ hmm_status hmm_dns_init(const hmm_dns_params* params, void* cuda_stream, void** 
   h->p = p;
   h->terms.assign(p.terms, p.terms + p.n_terms);
   h->p.terms = nullptr;
-  h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->user = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->d = p.dim;
   h->order = order;
   h->precision = p.precision;
@@ -520,6 +586,9 @@ hmm_status hmm_dns_init(const hmm_dns_params* params, void* cuda_stream, void** 
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cuda_fail(h, e, "hmm_dns_init allocation");
     return bail(e == cudaErrorMemoryAllocation ? HMM_ERR_OUT_OF_MEMORY : HMM_ERR_CUDA);
@@ -549,7 +618,9 @@ hmm_status hmm_dns_set_face_table(void* handle, const double* table_host, long l
   } else {
     std::copy(table_host, table_host + G, f64.begin());
   }
+  DNS_CUDA(h, cudaStreamSynchronize(h->stream));
   DNS_TRY(upload_faces(h, f64));
+  drop_graphs(h);                 // the graphs hold the old time step
   h->a_max = amax;
   DNS_TRY(pick_dt(h));
   h->j = 0;
@@ -603,7 +674,6 @@ void hmm_dns_destroy(void* handle) {
   DnsHandle* h = as_handle(handle);
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  else cudaDeviceSynchronize();
   free_all(h);
   delete h;
 }

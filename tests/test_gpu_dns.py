@@ -88,9 +88,11 @@ def test_dns_long_run(torch_cuda, precision):
 def test_dns_calls_continue_one_trajectory(torch_cuda, precision):
     cfg = _cfg((30, 41), 4)
     M0 = W.dns_initial(cfg, noise=0.2, seed=11)
-    M1, _ = _gpu(torch_cuda, cfg, M0, 9, precision)
-    M2, info = _gpu(torch_cuda, cfg, M0, 9, precision, calls=[1, 0, 3, 5])
-    assert info["j"] == 9
+    # one call of 33 steps (graph replays of six) against calls that start the
+    # six-step graphs at other phases of the state ping-pong and history ring
+    M1, _ = _gpu(torch_cuda, cfg, M0, 33, precision)
+    M2, info = _gpu(torch_cuda, cfg, M0, 33, precision, calls=[1, 0, 3, 5, 7, 11, 6])
+    assert info["j"] == 33
     assert np.abs(M1 - M2).max() <= (0.0 if precision == 0 else 1e-15)
 
 
