@@ -10,6 +10,11 @@ the batched FP32 form; the plain FP64 method is timed on the same workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The line also carries a "dns" object: the direct simulation resolving eps
+(Section 5's reference solver) on the paper's quasi-periodic 2D grid (1500^2),
+point-steps/s of the float-float FP32 form against the measured HBM bandwidth,
+and the FP64 form beside it (--no-dns leaves it out; --dns prints it alone).
+
 Multi-GPU: each rank runs an independent replica (the micro problems of one
 macro grid are independent; no collective on the data path), the value is
 the total over ranks divided by the slowest rank's time (weak scaling).
@@ -41,17 +46,19 @@ FP32_LANES_PER_SM = 128
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "micro_fp32_2d_c2_traffic.txt")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", "micro_fp32_2d.cuh")
+DNS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dns_kernel_quasi2d_traffic.txt")
+DNS_KERNEL_SOURCE = os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", "dns_kernels.cuh")
 
 
-def _traffic_from_profile():
+def _traffic_from_profile(traffic_file=None, kernel_source=None):
     """ncu DRAM bytes per full launch recorded for this kernel source, else None.
 
     The profile summary carries the SHA-256 of the kernel source it was captured
     from; once the source changes the figure no longer applies and None is returned.
     """
     try:
-        kv = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line)
-        sha = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        kv = dict(line.split(":", 1) for line in open(traffic_file or TRAFFIC_FILE) if ":" in line)
+        sha = hashlib.sha256(open(kernel_source or KERNEL_SOURCE, "rb").read()).hexdigest()
         if kv["kernel_source_sha256"].strip() != sha:
             return None
         return float(kv["dram_bytes_per_full_launch"])
@@ -283,6 +290,21 @@ def run_ours(args, rank, world, local_rank):
                          f"{args.cpu_workers} spawned processes, {info['wall_s']:.1f} s wall"}
     h32.close()
 
+    dns = None
+    if rank == 0 and not args.no_dns:
+        # the direct simulation resolving eps (Section 5's reference solver) on the
+        # paper's quasi-periodic 2D grid: float-float FP32 form and FP64 form
+        r32 = dns_measure(DNS_WORKLOAD, "fp32", 2004, 50)
+        r64 = dns_measure(DNS_WORKLOAD, "fp64", 204, 50)
+        hbm = _peaks().get("hbm_gbs", 6800.0)
+        dns = {k: r32[k] for k in ("workload", "grid", "value", "unit", "ms_per_step", "steps", "dt",
+                                   "bytes_per_point_step", "achieved_gbs", "achieved_gbs_without_coefficient")}
+        dns["roofline"] = {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                           "frac": r32["achieved_gbs"] / hbm,
+                           "traffic": _traffic_from_profile(DNS_TRAFFIC_FILE, DNS_KERNEL_SOURCE)}
+        dns["fp64"] = {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"]}
+        dns["speedup_vs_fp64"] = r32["value"] / r64["value"]
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -299,6 +321,7 @@ def run_ours(args, rank, world, local_rank):
             "fp32_vs_fp64_rel_err": rel,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": 3 * args.steps,
+            "dns": dns,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -440,8 +463,9 @@ def run_dns(args, local_rank):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     rec.update(r32)
+    traffic = _traffic_from_profile(DNS_TRAFFIC_FILE, DNS_KERNEL_SOURCE) if wl == DNS_WORKLOAD and not args.macro_grid else None
     rec["roofline"] = {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                       "frac": r32["achieved_gbs"] / hbm, "traffic": None,
+                       "frac": r32["achieved_gbs"] / hbm, "traffic": traffic,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
     if r64:
         rec["fp64"] = r64
@@ -504,6 +528,8 @@ def main():
     ap.add_argument("--micro-stepper", type=int, default=0, help="with --micro-only: 0 HeunP, 1 RK4P")
     ap.add_argument("--cpu-baseline-micro", action="store_true",
                     help="with --micro-only: also time the oracle on a sample of the boxes")
+    ap.add_argument("--no-dns", action="store_true",
+                    help="leave the direct-simulation measurement out of the default line")
     ap.add_argument("--dns", action="store_true",
                     help="time the direct simulation (--workload dns_*, --macro-grid for its grid, "
                          "--steps MPEA steps, --fp64-steps for the FP64 form)")
