@@ -474,7 +474,7 @@ def _interior(arr: np.ndarray, d: int, r: int) -> Tuple:
 
 def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: float,
                 M: int, alpha_micro: float, W: np.ndarray, w: np.ndarray, order: int,
-                trace: bool = False, stepper: int = 0):
+                trace: bool = False, stepper: int = 0, flux: Optional[Tuple[int, np.ndarray]] = None):
     """One batch of micro problems with a common grid; returns H_avg (B, 3).
 
     m_init: (B, 3, N, ..., N). The micro problem (eq. micro) is stepped by HeunP
@@ -488,6 +488,11 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
     The average (eq. upscaling) is sum_n w_n sum_xi W(xi) H(m^n)(xi), with
     H(m^n) the stage-1 field of step n (reading G8); w_0 = w_M = 0.
     W is the (N-2r)^d tensor of interior spatial weights.
+
+    With ``flux = (k, Wf)`` the averaged quantity is instead the flux a^eps D_s m
+    along axis k at that axis's faces (the flux model, Section 2.2): Wf is the
+    weight tensor over the faces face_gradient returns along k and all nodes
+    along the other axes.
     """
     d = len(afaces)
     r = 1 if order == 2 else 3
@@ -495,13 +500,25 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
     m = m_init.copy()
     inner = _interior(m, d, r)
     S = np.zeros(m.shape[:cax] + (3,), dtype=m.dtype)
-    Wb = W[(None,) * (cax + 1)]
+    Wb = W[(None,) * (cax + 1)] if W is not None else None
     red = tuple(range(cax + 1, m.ndim))
     energies, normdev = [], []
+    if flux is not None:
+        fk, Wf = flux
+        fax = cax + 1 + fk
+        Nk = m.shape[fax]
+        af = afaces[fk]
+        if af.ndim == m.ndim - 1:
+            af = np.expand_dims(af, cax)
+        af = _take(af, fax, 0, Nk - 1) if order == 2 else _take(af, fax, 1, Nk - 2)
+        Wfb = Wf[(None,) * (cax + 1)]
     for n in range(M + 1):
         H1 = field_H(m, afaces, dx, order)
         if w[n] != 0.0:
-            S += w[n] * (Wb * H1).sum(axis=red)
+            if flux is None:
+                S += w[n] * (Wb * H1).sum(axis=red)
+            else:
+                S += w[n] * (Wfb * (af * face_gradient(m, fax, dx, order))).sum(axis=red)
         if trace:
             energies.append(exchange_energy(m, afaces, dx, order))
             normdev.append(np.abs(np.sqrt((m ** 2).sum(cax)) - 1.0).max())

@@ -65,6 +65,8 @@ class HMMConfig:
     stencil_order            2 or 4
     precision                0: plain FP64 method, 1: batched FP32 form
     micro_stepper            0: HeunP, 1: RK4P (Section 3.1) for the micro problems
+    model                    0: field model (H_avg), 1: flux model (F_avg at staggered
+                             points, its macro divergence in place of H_avg; Section 2.2)
     coef_fn                  a coefficient that is not a sum of separable terms:
                              coef_fn(X, eps) -> a at the points X (a list of d
                              coordinate arrays); replaces c0 + terms when set
@@ -93,6 +95,7 @@ class HMMConfig:
     stencil_order: int = 4
     precision: int = 0
     micro_stepper: int = 0
+    model: int = 0
     coef_fn: Optional[Callable] = None
     name: str = ""
 
