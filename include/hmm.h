@@ -59,6 +59,19 @@ typedef enum {
   HMM_RK4P = 1
 } hmm_micro_stepper;
 
+/* The HMM macro model (Section 2.2). The field model averages H = div(a^eps grad m)
+ * over each micro problem (eq. upscaling) and steps eq. macro_disc with it. The
+ * flux model (eq. macro_flux) averages the flux a^eps grad m instead: column k of
+ * F_avg at the staggered point x_i + (DX_k/2) e_k, from a micro problem centred
+ * there (d micro problems per macro point), and steps the macro equation with
+ * div F_avg, the staggered difference of order interp_order (2 or 4) of those
+ * columns, in place of H_avg. The flux model runs in the FP64 form (HMM_FP64_PLAIN)
+ * on the separable coefficient terms. */
+typedef enum {
+  HMM_FIELD_MODEL = 0,
+  HMM_FLUX_MODEL = 1
+} hmm_model;
+
 /* One term of the material coefficient (Section 2.1 (A1); the examples of
  * Section 2.4 and Section 5 are sums of such terms):
  *     amp * prod_{k<d} g_k(2*pi*omega[k]*s_k + phase[k]),
@@ -108,7 +121,8 @@ typedef struct {
                                    arena kernel), 1 generic, 2 resident            */
   int micro_stepper;            /* hmm_micro_stepper; RK4P runs on the generic
                                    kernels (kernel_variant 0 selects them)         */
-  int reserved[3];              /* must be zero                                    */
+  int model;                    /* hmm_model                                       */
+  int reserved[2];              /* must be zero                                    */
 } hmm_params;
 
 /* Set-up (host only, plus device allocations on the current device).
@@ -131,8 +145,16 @@ hmm_status hmm_init(const hmm_params* params, void* cuda_stream, void** handle_o
  * ring (Section 4.2), and reduce H = div(a^eps grad m) by the kernel-weighted
  * average (eq. upscaling) into H_avg,i. M_dev and Havg_dev: SoA 3 x P FP64
  * device buffers; Havg_dev is overwritten. Pure: the macro history is not
- * touched. Returns HMM_ERR_NONFINITE if a micro state blew up. */
+ * touched. Returns HMM_ERR_NONFINITE if a micro state blew up.
+ * With the flux model, Havg_dev receives div F_avg (see hmm_model). */
 hmm_status hmm_micro_batch(void* handle, const double* M_dev, double* Havg_dev);
+
+/* Flux model only: the averaged fluxes themselves. F_dev: d x 3 x P FP64 device
+ * buffer; entry [(k*3 + c)*P + p] is component c of column k of F_avg at
+ * x_p + (DX_k/2) e_k, averaging a^eps D_s m along axis k over that axis's faces
+ * with the spatial kernel at the face positions. HMM_ERR_INVALID_ARG for a
+ * field-model handle. */
+hmm_status hmm_flux_batch(void* handle, const double* M_dev, double* F_dev);
 
 /* As hmm_micro_batch, with host buffers: copies M_host to the device, runs the
  * batch and copies H_avg back, all on the handle's stream. */

@@ -23,7 +23,7 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
             "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
             "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
-            "hmm_last_error", "hmm_destroy")
+            "hmm_flux_batch", "hmm_last_error", "hmm_destroy")
 # The symbols include/hmm_dns.h declares.
 EXPORTED_DNS = ("hmm_dns_init", "hmm_dns_set_face_table", "hmm_dns_step", "hmm_dns_step_host",
                 "hmm_dns_reset", "hmm_dns_info", "hmm_dns_last_error", "hmm_dns_destroy")
@@ -42,7 +42,7 @@ class HmmParams(ctypes.Structure):
                 ("pts_per_eps", c_double), ("mu_over_eps", c_double), ("micro_steps", c_int),
                 ("dt_safety", c_double), ("px", c_int), ("qx", c_int), ("pt", c_int), ("qt", c_int),
                 ("interp_order", c_int), ("stencil_order", c_int), ("precision", c_int),
-                ("kernel_variant", c_int), ("micro_stepper", c_int), ("reserved", c_int * 3)]
+                ("kernel_variant", c_int), ("micro_stepper", c_int), ("model", c_int), ("reserved", c_int * 2)]
 
 
 class HmmDnsParams(ctypes.Structure):
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_init.argtypes = [POINTER(HmmParams), c_void_p, POINTER(c_void_p)]
     lib.hmm_micro_batch.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.hmm_micro_batch_host.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.hmm_flux_batch.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.hmm_macro_step.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_macro_step_host.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_get_state.argtypes = [c_void_p, c_void_p, POINTER(c_longlong)]
@@ -149,6 +150,7 @@ def make_params(cfg, precision=None, kernel_variant=0):
     p.precision = int(cfg.precision if precision is None else precision)
     p.kernel_variant = int(kernel_variant)
     p.micro_stepper = int(getattr(cfg, "micro_stepper", 0))
+    p.model = int(getattr(cfg, "model", 0))
     return p, keep
 
 
@@ -233,6 +235,18 @@ class HMM:
         if out is None:
             out = torch.empty_like(M)
         self._check(self.lib.hmm_micro_batch(self.h, c_void_p(M.data_ptr()), c_void_p(self._field(out).data_ptr())))
+        return out
+
+    def flux_batch(self, M, out=None):
+        """Flux model: the averaged flux columns F_avg, (d, 3, P) (see hmm_flux_batch)."""
+        import torch
+        M = self._field(M)
+        d = int(self.cfg.dim)
+        if out is None:
+            out = torch.empty((d, 3, self.P), dtype=torch.float64, device=M.device)
+        if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and tuple(out.shape) == (d, 3, self.P)):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of shape ({d}, 3, {self.P})")
+        self._check(self.lib.hmm_flux_batch(self.h, c_void_p(M.data_ptr()), c_void_p(out.data_ptr())))
         return out
 
     def micro_batch_host(self, M, out):

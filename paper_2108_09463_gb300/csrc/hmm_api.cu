@@ -266,6 +266,8 @@ struct HmmHandle {
   double dt_macro = 0;
   // device
   BoxDesc* d_boxes = nullptr;
+  int nb = 0;                      // boxes: P (field model) or d P (flux model)
+  double* d_F = nullptr;           // flux model: F_avg, d x 3 x P
   double* d_W64 = nullptr;
   float* d_W32 = nullptr;
   double* d_w64 = nullptr;
@@ -318,7 +320,7 @@ hmm_status cuda_fail(HmmHandle* h, cudaError_t e, const char* where) {
 
 void free_all(HmmHandle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* ptrs[] = {h->d_boxes, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue, h->d_items, h->d_faces, h->d_face_off,
+  void* ptrs[] = {h->d_boxes, h->d_F, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue, h->d_items, h->d_faces, h->d_face_off,
                   h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -335,8 +337,14 @@ int max_n_for_dim(int d) { return d == 1 ? 1024 : (d == 2 ? 256 : 64); }
 hmm_status build(HmmHandle* h) {
   hmm_params& p = h->p;
   if (p.dim < 1 || p.dim > 3) return fail(h, HMM_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (p.reserved[i] != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.model != HMM_FIELD_MODEL && p.model != HMM_FLUX_MODEL)
+    return fail(h, HMM_ERR_INVALID_ARG, "model must be 0 (field) or 1 (flux)");
+  if (p.model == HMM_FLUX_MODEL && p.precision != HMM_FP64_PLAIN)
+    return fail(h, HMM_ERR_INVALID_ARG, "the flux model runs in the FP64 form (precision HMM_FP64_PLAIN)");
+  if (p.model == HMM_FLUX_MODEL && p.kernel_variant == 2)
+    return fail(h, HMM_ERR_INVALID_ARG, "the flux model runs on the generic kernel");
   if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
     return fail(h, HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
   h->dim = p.dim;
@@ -409,25 +417,32 @@ hmm_status build(HmmHandle* h) {
 
   // Boxes.
 
+  // Field model: one box per macro point. Flux model: one box per macro point
+  // and axis k, centred at x_i + (DX_k/2) e_k (the staggered point of column k).
+  const bool flux = p.model == HMM_FLUX_MODEL;
+  const int naxes = flux ? h->dim : 1;
+  h->nb = h->P * naxes;
   const int nlim = max_n_for_dim(h->dim);
   std::map<int, int> class_ofs;
   std::vector<double> W64;
-  h->boxes.resize(h->P);
+  h->boxes.resize(h->nb);
   h->box_dt.resize(h->P);
   h->box_mu.resize(h->P);
   h->box_dx.resize(h->P);
   h->box_n.resize(h->P);
   h->nmax = 0;
   h->lu_per_batch = 0;
-  for (int pi = 0; pi < h->P; ++pi) {
+  for (int bi = 0; bi < h->nb; ++bi) {
+    const int pi = bi % h->P;
     BoxDesc bd{};
     bd.p = pi;
+    bd.fax = flux ? bi / h->P : -1;
     int rem = pi;
     for (int k = h->dim - 1; k >= 0; --k) {
       bd.ci[k] = rem % h->nmac[k];
       rem /= h->nmac[k];
     }
-    for (int k = 0; k < h->dim; ++k) bd.xc[k] = bd.ci[k] * h->DX[k];
+    for (int k = 0; k < h->dim; ++k) bd.xc[k] = bd.ci[k] * h->DX[k] + (k == bd.fax ? 0.5 * h->DX[k] : 0.0);
     bd.eps = h->eps_field.empty() ? p.eps : h->eps_field[pi];
     bd.N = h->n_field.empty() ? p.box_n : h->n_field[pi];
     if (!(bd.eps > 0)) return fail(h, HMM_ERR_INVALID_ARG, "eps must be > 0");
@@ -454,10 +469,24 @@ hmm_status build(HmmHandle* h) {
       for (int jn = 0; jn < h->radius; ++jn)
         if (W64[ofs + jn] != 0.0 || W64[ofs + bd.N - 1 - jn] != 0.0)
           return fail(h, HMM_ERR_INVALID_ARG, "averaging box [-mu, mu] reaches the Dirichlet ring");
+      if (flux) {
+        // the flux model's face weights K(xi_f/mu), xi_f = xi_j + dx/2, j = 0..N-2,
+        // normalised (entry N-1 unused); with the ring off the averaging box only
+        // faces that touch an interior node carry weight
+        double sf = 0;
+        for (int jn = 0; jn < bd.N; ++jn) {
+          const double xf = (jn + 0.5 - (bd.N - 1) / 2.0) * bd.dx;
+          const double v = jn < bd.N - 1 ? host::eval_kernel(cK, p.px, p.qx, xf / mu) : 0.0;
+          W64.push_back(v);
+          sf += v;
+        }
+        if (!(sf != 0)) return fail(h, HMM_ERR_INVALID_ARG, "face weights vanish (mu too small)");
+        for (int jn = 0; jn < bd.N; ++jn) W64[ofs + bd.N + jn] /= sf;
+      }
       it = class_ofs.emplace(bd.N, ofs).first;
     }
     bd.wofs = it->second;
-    h->boxes[pi] = bd;
+    h->boxes[bi] = bd;
     h->box_dt[pi] = bd.dt;
     h->box_mu[pi] = mu;
     h->box_dx[pi] = bd.dx;
@@ -489,13 +518,13 @@ hmm_status build(HmmHandle* h) {
       om32[j] = (float)tail;
     }
   }
-  HMM_CUDA(h, cudaMalloc(&h->d_boxes, sizeof(BoxDesc) * h->P));
+  HMM_CUDA(h, cudaMalloc(&h->d_boxes, sizeof(BoxDesc) * h->nb));
   HMM_CUDA(h, cudaMalloc(&h->d_W64, sizeof(double) * W64.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_W32, sizeof(float) * W32.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_w64, sizeof(double) * w.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_w32, sizeof(float) * w32.size()));
   HMM_CUDA(h, cudaMalloc(&h->d_om32, sizeof(float) * om32.size()));
-  HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->P, cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->nb, cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_W64, W64.data(), sizeof(double) * W64.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_W32, W32.data(), sizeof(float) * W32.size(), cudaMemcpyHostToDevice));
   HMM_CUDA(h, cudaMemcpy(h->d_w64, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
@@ -511,6 +540,7 @@ hmm_status build(HmmHandle* h) {
   HMM_CUDA(h, cudaMemset(h->d_hist, 0, 2 * f3));
   HMM_CUDA(h, cudaMalloc(&h->d_acc, f3));
   HMM_CUDA(h, cudaMalloc(&h->d_stage, f3));
+  if (flux) HMM_CUDA(h, cudaMalloc(&h->d_F, f3 * h->dim));
   HMM_CUDA(h, cudaEventCreate(&h->ev0));
   HMM_CUDA(h, cudaEventCreate(&h->ev1));
   HMM_CUDA(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
@@ -547,12 +577,13 @@ hmm_status build(HmmHandle* h) {
                                                   : micro_slot_bytes_fp32(h->dim, h->nmax);
   }
   if (per_sm < 1) return fail(h, HMM_ERR_INVALID_ARG, "micro kernel does not fit on an SM for this box size");
-  h->grid = h->res2d ? res2d_max_grid(h->plan) : std::min(h->P, per_sm * h->num_sms);
+  h->grid = h->res2d ? res2d_max_grid(h->plan) : std::min(h->nb, per_sm * h->num_sms);
   HMM_CUDA(h, cudaMalloc(&h->d_arena, h->slot_bytes * (size_t)h->grid));
 
   MicroArgs& a = h->args;
   a.boxes = h->d_boxes;
-  a.n_boxes = h->P;
+  a.n_boxes = h->nb;
+  a.Fout = h->d_F;
   a.queue = h->d_queue;
   a.err = h->d_err;
   a.P = h->P;
@@ -599,6 +630,10 @@ hmm_status enqueue_micro(HmmHandle* h, const double* M, double* Havg) {
                       ? launch_micro_fp64(a, h->dim, h->radius, h->grid, h->block, h->smem, h->stream)
                       : launch_micro_fp32(a, h->dim, h->radius, h->grid, h->block, h->smem, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "micro kernel launch");
+  if (h->p.model == HMM_FLUX_MODEL && Havg) {
+    e = launch_flux_divergence(h->d_F, Havg, h->dim, h->nmac, h->DX, h->p.interp_order, h->P, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "flux divergence launch");
+  }
   return HMM_OK;
 }
 
@@ -718,6 +753,26 @@ hmm_status hmm_micro_batch(void* handle, const double* M_dev, double* Havg_dev) 
   return s;
 }
 
+hmm_status hmm_flux_batch(void* handle, const double* M_dev, double* F_dev) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_dev || !F_dev) return fail(h, HMM_ERR_INVALID_ARG, "null device pointer");
+  if (h->p.model != HMM_FLUX_MODEL) return fail(h, HMM_ERR_INVALID_ARG, "hmm_flux_batch needs a flux-model handle");
+  HMM_TRY(begin_call(h));
+  HMM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  hmm_status s = enqueue_micro(h, M_dev, nullptr);
+  if (s != HMM_OK) return s;
+  HMM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  HMM_CUDA(h, cudaMemcpyAsync(F_dev, h->d_F, sizeof(double) * 3 * (size_t)h->P * h->dim, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  HMM_TRY(end_call(h));
+  s = check_error_word(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->last_ms = ms;
+  return s;
+}
+
 hmm_status hmm_micro_batch_host(void* handle, const double* M_host, double* Havg_host) {
   HmmHandle* h = as_handle(handle);
   if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
@@ -823,6 +878,8 @@ hmm_status hmm_set_face_table(void* handle, const double* table_host, long long 
   HmmHandle* h = as_handle(handle);
   if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
   if (!table_host) return fail(h, HMM_ERR_INVALID_ARG, "null face table");
+  if (h->p.model == HMM_FLUX_MODEL)
+    return fail(h, HMM_ERR_INVALID_ARG, "tabulated coefficients are not available with the flux model");
   const int d = h->dim;
   std::vector<long long> off(h->P);
   long long total = 0;
@@ -874,7 +931,7 @@ hmm_status hmm_set_face_table(void* handle, const double* table_host, long long 
     bd.dt = host::micro_dt(p.dt_safety, p.alpha_micro, bmax[bd.p], d, p.stencil_order, bd.dx, p.micro_stepper);
     h->box_dt[bd.p] = bd.dt;
   }
-  HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->P, cudaMemcpyHostToDevice));
+  HMM_CUDA(h, cudaMemcpy(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * h->nb, cudaMemcpyHostToDevice));
   h->a_max = gmax;
   if (!(p.dt_macro > 0)) {
     double dX = h->DX[0];

@@ -32,7 +32,8 @@ struct BoxDesc {
   double eps;   // eps_i
   double dx;    // micro grid spacing
   double dt;    // micro time step
-  double xc[3]; // macro point coordinates x_i
+  double xc[3]; // box centre: x_i, or x_i + (DX_k/2) e_k for a flux box
+  int fax;      // flux model: the axis k of the flux column this box averages; -1: field model
 };
 
 struct MicroArgs {
@@ -42,6 +43,7 @@ struct MicroArgs {
   int* err;              // error word (bits above)
   const double* M;       // macro field, SoA 3 x P
   double* Havg;          // output, SoA 3 x P
+  double* Fout;          // flux model output, d x 3 x P
   int P;
   int nmac[3];
   double DX[3];
@@ -65,6 +67,10 @@ struct MicroArgs {
 };
 
 // Launchers (one per precision); dim in {1,2,3}, radius in {1,3}.
+// Flux model: H_i = sum_k D_k F_k, the staggered difference of order 2 or 4 of
+// the flux columns F (d x 3 x P, column k at x_i + (DX_k/2) e_k), periodic.
+cudaError_t launch_flux_divergence(const double* F, double* H, int dim, const int* nmac, const double* DX,
+                                   int order, int P, cudaStream_t st);
 cudaError_t launch_micro_fp64(const MicroArgs& a, int dim, int radius, int grid, int block,
                               size_t smem, cudaStream_t st);
 cudaError_t launch_micro_fp32(const MicroArgs& a, int dim, int radius, int grid, int block,

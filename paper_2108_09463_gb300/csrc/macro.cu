@@ -109,7 +109,51 @@ __global__ void check_finite_kernel(const double* x, int n, int* err) {
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonFinite);
 }
 
+// Flux model (eq. macro_flux): H_i = sum_k D_k F_k at macro point i, F_k's entry i
+// the flux column k at x_i + (DX_k/2) e_k. Order 4: (F_{i-3/2} - 27 F_{i-1/2} +
+// 27 F_{i+1/2} - F_{i+3/2}) / (24 DX_k); order 2: (F_{i+1/2} - F_{i-1/2}) / DX_k;
+// indices periodic.
+__global__ void flux_div_kernel(const double* F, double* H, int dim, int n0, int n1, int n2,
+                                double DX0, double DX1, double DX2, int order, int P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int nm[3] = {n0, n1, n2};
+  const double DX[3] = {DX0, DX1, DX2};
+  int ci[3] = {0, 0, 0}, rem = p;
+  for (int k = dim - 1; k >= 0; --k) {
+    ci[k] = rem % nm[k];
+    rem /= nm[k];
+  }
+  double out[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < dim; ++k) {
+    // linear index of the point shifted by s along axis k (periodic)
+    int stride = 1;
+    for (int a = dim - 1; a > k; --a) stride *= nm[a];
+    auto at = [&](int s) {
+      int i = (ci[k] + s) % nm[k];
+      if (i < 0) i += nm[k];
+      return p + (i - ci[k]) * stride;
+    };
+    const double* Fk = F + (size_t)k * 3 * P;
+    for (int c = 0; c < 3; ++c) {
+      const double* f = Fk + (size_t)c * P;
+      double v;
+      if (order == 2) v = (f[at(0)] - f[at(-1)]) / DX[k];
+      else v = (((f[at(-2)] - 27.0 * f[at(-1)]) + 27.0 * f[at(0)]) - f[at(1)]) / (24.0 * DX[k]);
+      out[c] += v;
+    }
+  }
+  for (int c = 0; c < 3; ++c) H[(size_t)c * P + p] = out[c];
+}
+
 static inline int nblk(int P) { return (P + 255) / 256; }
+
+cudaError_t launch_flux_divergence(const double* F, double* H, int dim, const int* nmac, const double* DX,
+                                   int order, int P, cudaStream_t st) {
+  flux_div_kernel<<<nblk(P), 256, 0, st>>>(F, H, dim, nmac[0], dim > 1 ? nmac[1] : 1, dim > 2 ? nmac[2] : 1,
+                                           DX[0], dim > 1 ? DX[1] : 1.0, dim > 2 ? DX[2] : 1.0, order, P);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_h_term(const double* M, const double* H, double alpha, double* h, int P,
                           cudaStream_t st) {

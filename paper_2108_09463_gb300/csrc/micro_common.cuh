@@ -133,10 +133,11 @@ template <int D>
 __device__ void box_setup_tables(const MicroArgs& a, const BoxDesc& bd, const SetupSmem& sm) {
   const int N = bd.N, k = a.interp_k, w = 2 * k + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // Lagrange basis l_a(s), s = xi_j / DX, nodes -k..k (Section 4.1).
+  // Lagrange basis l_a(s), s = xi_j / DX, nodes -k..k (Section 4.1); a flux box
+  // centred at x_i + (DX_k/2) e_k evaluates the same interpolant at s + 1/2 on axis k.
   for (int e = tid; e < D * N; e += nt) {
     const int ax = e / N, j = e - ax * N;
-    const double s = node_offset(2 * j, N, bd.dx) / a.DX[ax];
+    const double s = node_offset(2 * j, N, bd.dx) / a.DX[ax] + (ax == bd.fax ? 0.5 : 0.0);
     for (int ia = 0; ia < w; ++ia) {
       double v = 1.0;
       for (int ib = 0; ib < w; ++ib)

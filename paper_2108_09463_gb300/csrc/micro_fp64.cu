@@ -75,6 +75,26 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
     const double* W1 = a.W64 + bd.wofs;
     const int nint = ipow<D>(N - 2 * R);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    // Flux model: the box averages the face flux along axis fax (weights at the
+    // face positions follow the node weights in the table) instead of H.
+    const int fax = bd.fax;
+    const double* Wf1 = W1 + N;
+    const double cf = R == 3 ? 1.0 / (24.0 * bd.dx) : 1.0 / bd.dx;
+    const int nsite = fax >= 0 ? ipow<D>(N - 2 * R) / (N - 2 * R) * (N - 2 * R + 1) : 0;
+    auto flux_sum = [&](const double* u, double w, double& f0, double& f1, double& f2) {
+      for (int t = tid; t < nsite; t += nt) {
+        int j[3];
+        const int idx = flux_site<D, R>(t, N, fax, j);
+        double F[3];
+        face_flux<R, double>(u, af + (size_t)fax * cap, cap, idx, st.s[fax], cf, F);
+        double W = w;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) W *= ax == fax ? Wf1[j[ax]] : W1[j[ax]];
+        f0 += W * F[0];
+        f1 += W * F[1];
+        f2 += W * F[2];
+      }
+    };
 
     // H(m_init) and its weighted sum (times sum_n w_n).
     {
@@ -96,6 +116,10 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
       }
       double wsum = 0.0;
       for (int n = 0; n <= a.msteps; ++n) wsum += a.w64[n];
+      if (fax >= 0) {             // the flux of m_init instead of H(m_init)
+        s0 = s1 = s2 = 0.0;
+        flux_sum(mi, 1.0, s0, s1, s2);
+      }
       acc0 = s0 * wsum;
       acc1 = s1 * wsum;
       acc2 = s2 * wsum;
@@ -105,12 +129,14 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
     for (int n = 0; n <= a.msteps; ++n) {
       const double wn = a.w64[n];
       if (n == a.msteps && wn == 0.0) break;  // K0(1) = 0: no final stencil pass
+      if (fax >= 0 && wn != 0.0) flux_sum(vA, wn, acc0, acc1, acc2);   // v^n is read-only in stage 1
+      if (fax >= 0 && n == a.msteps) break;
       // Stage 1: H(m^n) = H(m_init) + H(v^n), its weighted sum, k1, v + dt k1, v + dt/2 k1.
       for (int t = tid; t < nint; t += nt) {
         const int idx = interior_node<D, R>(t, N);
         double Hv[3];
         stencil_H<D, R, double>(vA, af, cap, st, idx, cs, Hv);
-        if (wn != 0.0) {
+        if (fax < 0 && wn != 0.0) {
           int j[3];
           node_coords<D>(idx, N, j);
           double W = W1[j[0]];
@@ -193,9 +219,10 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
     }
     block_sum3(acc0, acc1, acc2, sm.red);
     if (tid == 0) {
-      a.Havg[bd.p] = acc0;
-      a.Havg[a.P + bd.p] = acc1;
-      a.Havg[2 * a.P + bd.p] = acc2;
+      double* out = fax >= 0 ? a.Fout + (size_t)fax * 3 * a.P : a.Havg;
+      out[bd.p] = acc0;
+      out[a.P + bd.p] = acc1;
+      out[2 * a.P + bd.p] = acc2;
       if (!(isfinite(acc0) && isfinite(acc1) && isfinite(acc2))) atomicOr(a.err, kErrNonFinite);
     }
   }

@@ -61,6 +61,7 @@ __global__ void noalloc_boxes_kernel(BoxDesc* boxes, int P, int dim, int n0, int
   bd.eps = eps;
   bd.dx = dx;
   bd.dt = dt;
+  bd.fax = -1;
   boxes[p] = bd;
 }
 
@@ -108,8 +109,9 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point runs the FP32 form only");
   if (p.eps_field || p.box_n_field)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point needs uniform eps and N");
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (p.reserved[i] != 0) return noalloc_fail(HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.model != HMM_FIELD_MODEL) return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free batch runs the field model");
   if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
   if (p.kernel_variant != 0 && p.kernel_variant != 1)

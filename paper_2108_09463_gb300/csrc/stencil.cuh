@@ -45,6 +45,42 @@ __device__ __forceinline__ void stencil_H(const T* __restrict__ m, const T* __re
   }
 }
 
+// Flux model sites: the faces along axis k that touch an interior node, faces
+// j_k + 1/2 with j_k = R-1 .. N-R-1, at interior nodes along the other axes;
+// t in [0, (N-2R+1)(N-2R)^(D-1)). Returns the index of the face's lower node and
+// its per-axis node coordinates in j.
+template <int D, int R>
+__device__ __forceinline__ int flux_site(int t, int N, int k, int* j) {
+  const int Ni = N - 2 * R, Nk = Ni + 1;
+  int rem = t, idx = 0;
+#pragma unroll
+  for (int ax = D - 1; ax >= 0; --ax) {
+    const int n = ax == k ? Nk : Ni;
+    const int q = rem % n;
+    rem /= n;
+    j[ax] = ax == k ? q + R - 1 : q + R;
+  }
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) idx = idx * N + j[ax];
+  return idx;
+}
+
+// The face flux a_f D_s m along axis k (stride s) at the face between node idx
+// and idx + s, times 1/(24 dx) (order 4) or 1/dx (order 2) ("cf"), 3 components.
+template <int R, typename T>
+__device__ __forceinline__ void face_flux(const T* __restrict__ m, const T* __restrict__ ak, size_t cap, int idx,
+                                          int s, T cf, T* F) {
+  const T a = ak[idx] * cf;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T* mc = m + c * cap;
+    T g;
+    if (R == 1) g = mc[idx + s] - mc[idx];
+    else g = (mc[idx - s] - mc[idx + 2 * s]) + T(27) * (mc[idx + s] - mc[idx]);
+    F[c] = a * g;
+  }
+}
+
 // f = -m x H - alpha m x (m x H)   (Section 3.1)
 template <typename T>
 __device__ __forceinline__ void ll_rhs(const T* m, const T* H, T alpha, T* f) {
