@@ -81,7 +81,11 @@ def _oracle_chunk(args):
     cfg = W.config(name, **over)
     M0 = W.initial_field(cfg)
     t = time.perf_counter()
-    O.micro_batch(cfg, M0, points=points)
+    if getattr(cfg, "model", 0) == 1:
+        from oracle import flux_oracle as F
+        F.micro_batch_flux(cfg, M0, points=points)
+    else:
+        O.micro_batch(cfg, M0, points=points)
     return time.perf_counter() - t
 
 
@@ -103,9 +107,10 @@ def oracle_sample(name: str, boxes_per_worker: int, workers: int, pool=None, ove
         pool.map(_oracle_chunk, chunks)
     wall = time.perf_counter() - t0
     lu = 0.0
+    boxes_per_point = cfg.dim if getattr(cfg, "model", 0) == 1 else 1   # the flux model: one box per axis
     for p in pts:
         g = O.box_geometry(cfg, p)
-        lu += (g["N"] - 2 * g["r"]) ** cfg.dim * g["M"]
+        lu += boxes_per_point * (g["N"] - 2 * g["r"]) ** cfg.dim * g["M"]
     return lu / wall, dict(boxes=n, wall_s=wall, lu=lu)
 
 
@@ -304,6 +309,9 @@ def run_ours(args, rank, world, local_rank):
                            "traffic": _traffic_from_profile(DNS_TRAFFIC_FILE, DNS_KERNEL_SOURCE)}
         dns["fp64"] = {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"]}
         dns["speedup_vs_fp64"] = r32["value"] / r64["value"]
+        if not args.no_cpu_baseline:
+            v, sample = dns_oracle_sample()
+            dns["cpu_baseline"] = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {
@@ -450,6 +458,23 @@ def dns_measure(workload=DNS_WORKLOAD, precision="fp32", steps=1000, warmup=50, 
             "finite": bool(torch.isfinite(M).all())}
 
 
+def dns_oracle_sample(workload=DNS_WORKLOAD, n=150, steps=8):
+    """Time the direct-simulation oracle on an n x n (n for 1D) grid of the same
+    coefficient and spacing scale, `steps` steps (the RK4P start-up included);
+    returns (point-steps/s, sample description). Single process (numpy)."""
+    import workloads as W
+    from oracle import dns_oracle as D
+    cfg = W.dns_config(workload)
+    cfg = cfg.replace(n=tuple([n] * cfg.dim + [1] * (3 - cfg.dim)))
+    M0 = W.dns_initial(cfg)
+    run = D.DNS(cfg, M0)
+    t = time.perf_counter()
+    run.step(steps)
+    wall = time.perf_counter() - t
+    return cfg.n_points * steps / wall, (f"{'x'.join(map(str, cfg.shape))} grid of {workload}'s coefficient, "
+                                         f"{steps} steps (2 RK4P + {steps - 2} MPEA), 1 process, {wall:.1f} s wall")
+
+
 def run_dns(args, local_rank):
     """--dns: one JSON line for the direct simulation (float-float FP32 form and
     the FP64 form on the same grid)."""
@@ -473,6 +498,9 @@ def run_dns(args, local_rank):
         rec["fp64"] = r64
         rec["speedup_vs_fp64"] = r32["value"] / r64["value"]
     rec["clocks"] = clk.summary()
+    if not args.no_cpu_baseline:
+        v, sample = dns_oracle_sample(wl)
+        rec["cpu_baseline"] = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
     print(json.dumps(rec), flush=True)
 
 
