@@ -65,8 +65,8 @@ typedef enum {
  * F_avg at the staggered point x_i + (DX_k/2) e_k, from a micro problem centred
  * there (d micro problems per macro point), and steps the macro equation with
  * div F_avg, the staggered difference of order interp_order (2 or 4) of those
- * columns, in place of H_avg. The flux model runs in the FP64 form (HMM_FP64_PLAIN)
- * on the separable coefficient terms. */
+ * columns, in place of H_avg. The flux model runs on the generic kernels (both
+ * precision forms; kernel_variant 0 or 1) with the separable coefficient terms. */
 typedef enum {
   HMM_FIELD_MODEL = 0,
   HMM_FLUX_MODEL = 1

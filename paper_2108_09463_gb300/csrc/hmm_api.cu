@@ -341,8 +341,6 @@ hmm_status build(HmmHandle* h) {
     if (p.reserved[i] != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
   if (p.model != HMM_FIELD_MODEL && p.model != HMM_FLUX_MODEL)
     return fail(h, HMM_ERR_INVALID_ARG, "model must be 0 (field) or 1 (flux)");
-  if (p.model == HMM_FLUX_MODEL && p.precision != HMM_FP64_PLAIN)
-    return fail(h, HMM_ERR_INVALID_ARG, "the flux model runs in the FP64 form (precision HMM_FP64_PLAIN)");
   if (p.model == HMM_FLUX_MODEL && p.kernel_variant == 2)
     return fail(h, HMM_ERR_INVALID_ARG, "the flux model runs on the generic kernel");
   if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
@@ -550,8 +548,9 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  std::string why = "the resident kernels need the FP32 form, HeunP and d = 2 or 3";
+  std::string why = "the resident kernels need the FP32 form, HeunP, the field model and d = 2 or 3";
   const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 && p.micro_stepper == HMM_HEUNP &&
+                      p.model == HMM_FIELD_MODEL &&
                       res2d_make_plan(h->dim, h->boxes.data(), h->P, h->radius, h->interp_k, p.n_terms,
                                       (size_t)optin - 256, &h->plan, &why) &&
                       (int)h->plan.groups.size() <= kQueues;

@@ -175,6 +175,29 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
     }
     double wsum = 0.0;
     for (int n = 0; n <= a.msteps; ++n) wsum += a.w64[n];
+    // Flux model: the box averages the face flux along axis fax instead of H (the
+    // face weights follow the node weights in the table); its m_init part in FP64.
+    const int fax = bd.fax;
+    const double cf = R == 3 ? 1.0 / (24.0 * bd.dx) : 1.0 / bd.dx;
+    const int nsite = fax >= 0 ? nint / (N - 2 * R) * (N - 2 * R + 1) : 0;
+    auto flux_sum = [&](const double* u, double& f0, double& f1, double& f2) {
+      for (int t = tid; t < nsite; t += nt) {
+        int j[3];
+        const int idx = flux_site<D, R>(t, N, fax, j);
+        double F[3];
+        face_flux<R, double>(u, sl.af64 + (size_t)fax * cap, cap, idx, st.s[fax], cf, F);
+        double W = 1.0;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) W *= ax == fax ? W1d[N + j[ax]] : W1d[j[ax]];
+        f0 += W * F[0];
+        f1 += W * F[1];
+        f2 += W * F[2];
+      }
+    };
+    if (fax >= 0) {
+      s0 = s1 = s2 = 0.0;
+      flux_sum(sl.mi64, s0, s1, s2);
+    }
     s0 *= wsum;
     s1 *= wsum;
     s2 *= wsum;
@@ -280,7 +303,20 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
     }
     // The final state's weight w_M (zero for K0 in K0^{p,q}) and the contraction with H(W).
     const float wM = a.w32[a.msteps];
-    for (int t = tid; t < nint; t += nt) {
+    if (fax >= 0) {
+      // Flux model: sum_n w_n F(v^n) = F(V), V = sum_n w_n v^n, the face flux of the
+      // accumulated state; V (zero on the ring) goes through the FP64 m_init scratch.
+      for (int idx = tid; idx < ntot; idx += nt) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t o = c * cap + idx;
+          sl.mi64[o] = ((double)sl.V[o] - (double)sl.Vc[o]) + (double)wM * (double)sl.vA[o];
+        }
+      }
+      __syncthreads();
+      flux_sum(sl.mi64, s0, s1, s2);
+    }
+    for (int t = tid; t < (fax >= 0 ? 0 : nint); t += nt) {
       const int idx = interior_node<D, R>(t, N);
       const double hw = stencil_of_weight<D, R>(W1d, sl.af64, cap, st, idx, N, cs64);
 #pragma unroll
@@ -295,9 +331,10 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
     }
     block_sum3(s0, s1, s2, sm.red);
     if (tid == 0) {
-      a.Havg[bd.p] = s0;
-      a.Havg[a.P + bd.p] = s1;
-      a.Havg[2 * a.P + bd.p] = s2;
+      double* out = fax >= 0 ? a.Fout + (size_t)fax * 3 * a.P : a.Havg;
+      out[bd.p] = s0;
+      out[a.P + bd.p] = s1;
+      out[2 * a.P + bd.p] = s2;
       if (!(isfinite(s0) && isfinite(s1) && isfinite(s2))) atomicOr(a.err, kErrNonFinite);
     }
   }

@@ -1,11 +1,11 @@
 """GPU parity of the flux model (Section 2.2, eq. macro_flux) against the oracle.
 
-The FP64 form (the only form the flux model runs in) is compared with the flux
-oracle evaluated in long double on sampled boxes (the raw flux columns, bound
-1e-12 relative to the largest column), with the FP64 oracle on the macro
-divergence that hmm_micro_batch returns for a flux-model handle (the divergence
-adds only a few roundings), and with the oracle's flux-model macro stepper over
-the RK4P start-up and MPEA steps.
+The FP64 form is compared with the flux oracle evaluated in long double on
+sampled boxes (the raw flux columns, bound 1e-12 relative to the largest
+column), the batched FP32 form with the FP64 oracle on every box (bound 1e-6);
+the macro divergence that hmm_micro_batch returns for a flux-model handle
+against the oracle's divergence of the same columns, and the macro steps
+against the oracle's flux-model stepper over the RK4P start-up and MPEA steps.
 """
 import numpy as np
 import pytest
@@ -55,6 +55,23 @@ def _cfg(case):
 def _points(cfg, k=4):
     P = cfg.n_points
     return sorted(set([0, P - 1, P // 2, P // 3]))[:k]
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_flux_columns_parity_fp32(torch_cuda, case):
+    from paper_2108_09463_gb300 import HMM
+    cfg = _cfg(case)
+    M0 = W.initial_field(cfg)
+    h = HMM(cfg, precision=1)
+    M = torch_cuda.from_numpy(M0).cuda()
+    Fg = h.flux_batch(M).cpu().numpy()
+    H = h.micro_batch(M).cpu().numpy()
+    h.close()
+    Fr = F.micro_batch_flux(cfg, M0)
+    err = np.abs(Fg - Fr).max() / np.abs(Fr).max()
+    assert err < 1e-6, (case, err)
+    Hr = F.flux_divergence(cfg, Fg)
+    assert np.abs(H - Hr).max() <= 1e-13 * np.abs(Hr).max()
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -115,7 +132,7 @@ def test_flux_model_validation(torch_cuda):
     from paper_2108_09463_gb300 import HMM, HmmError
     cfg = _cfg("2d")
     with pytest.raises(HmmError):
-        HMM(cfg, precision=1)
+        HMM(cfg, precision=1, kernel_variant=2)     # the resident kernels average H only
     h = HMM(cfg.replace(model=0), precision=0)
     with pytest.raises(HmmError):
         h.flux_batch(torch_cuda.from_numpy(W.initial_field(cfg)).cuda())
