@@ -206,15 +206,18 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   __shared__ R_ s_a[WK][TWO_D ? DEPTH : 1][2][32];
   __shared__ R_ s_h[WK][TWO_D ? HD : 1][2][3][32];
   const int q_first = r0 - RR, q_last = TWO_D ? r1 - 1 + RR : 0;
-  auto slot_of = [&](int q) { return (q - q_first) % DEPTH; };
-  auto face_row = [&](int q) { return wrap(ORDER == 4 ? q - 2 : q - 1); };
-  auto issue = [&](int q) {
+  // Rows are issued in increasing order q = q_first, q_first + 1, ...: their
+  // wrapped row and face row advance by one add and a compare per row, and the
+  // ring slot of the row being consumed rotates.
+  int irow = TWO_D ? wrap(q_first) : 0;
+  int ifrow = TWO_D ? wrap(ORDER == 4 ? q_first - 2 : q_first - 1) : 0;
+  int cslot = DEPTH - 1;                             // slot of the row last consumed
+  auto issue = [&](int q, int sl) {
     if (q <= q_last) {
-      const int sl = slot_of(q);
-      const long long idx = (long long)wrap(q) * n1 + xl;
+      const long long idx = (long long)irow * n1 + xl;
 #pragma unroll
       for (int c = 0; c < 3; ++c) cp_async(&s_st[wib][sl][c][lane], state + c * A.G + idx, 8);
-      if (q >= r0) cp_async(&s_a[wib][sl][1][lane], AY + (long long)face_row(q) * n1 + xl, (int)sizeof(R_));
+      if (q >= r0) cp_async(&s_a[wib][sl][1][lane], AY + (long long)ifrow * n1 + xl, (int)sizeof(R_));
       const int pr = q - RR;
       if (pr >= r0 && pr < r1) {
         const long long gi = (long long)pr * n1 + xl;
@@ -231,16 +234,18 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
       }
     }
     cp_async_commit();      // one group per row, empty past the last row
+    irow = irow + 1 == n0 ? 0 : irow + 1;
+    ifrow = ifrow + 1 == n0 ? 0 : ifrow + 1;
   };
   auto push_row = [&](int q) {
 #pragma unroll
     for (int k = 0; k < RR; ++k) win[k] = win[k + 1];
     if constexpr (TWO_D) {
+      cslot = cslot == DEPTH - 1 ? 0 : cslot + 1;    // row q's slot
       cp_async_wait<DEPTH - 2>();                    // row q's group is complete
-      const int sl = slot_of(q);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) win[RR].v[c] = s_st[wib][sl][c][lane];
-      issue(q + DEPTH - 1);                          // into the slot row q - 1 used
+      for (int c = 0; c < 3; ++c) win[RR].v[c] = s_st[wib][cslot][c][lane];
+      issue(q + DEPTH - 1, cslot == 0 ? DEPTH - 1 : cslot - 1);   // into the slot row q - 1 used
     } else {
       win[RR] = load_node<FF>(A, xl);
     }
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
   // y-face flux from the full window: order 4 the face between rows q-2 and q-1
   // (rows q-3..q), order 2 the face between rows q-1 and q
   auto push_face = [&](int q) {
-    const R_ ay = s_a[wib][slot_of(q)][1][lane];
+    const R_ ay = s_a[wib][cslot][1][lane];
 #pragma unroll
     for (int k = 0; k < RR; ++k)
 #pragma unroll
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
     const long long G = A.G;
     R_ ax, hp1[3], hp2[3];                           // a_x, h^{j-1}, h^{j-2}
     if constexpr (TWO_D) {
-      const int sl = slot_of(p + RR);                // arrived with state row p + R
+      const int sl = cslot;                          // arrived with state row p + R
       ax = s_a[wib][sl][0][lane];
       if constexpr (MODE != kField) {
 #pragma unroll
@@ -330,7 +335,9 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
       R_ b0 = w[1] * a2 - w[2] * a1;
       R_ b1 = w[2] * a0 - w[0] * a2;
       R_ b2 = w[0] * a1 - w[1] * a0;
-      R_ f = R_(2) / (R_(1) + (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+      R_ f;
+      if constexpr (FF) f = __fdividef(2.f, 1.f + (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));   // 2 ulp
+      else f = 2.0 / (1.0 + (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
       R_ dl[3] = {f * (a0 + b0), f * (a1 + b1), f * (a2 + b2)};
       bool bad = false;
       if constexpr (FF) {
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(32 * kWarps, (MODE == kMpeaFF) ? 7 : 4) dns_ke
     // rows r0-R..r0-1 fill the window; rows r0..r0+R-1 also push their faces;
     // from row r0+R on each new row completes row p = q - R (p in [r0, r1))
 #pragma unroll
-    for (int k = 0; k < DEPTH - 1; ++k) issue(q_first + k);
+    for (int k = 0; k < DEPTH - 1; ++k) issue(q_first + k, k);
     for (int q = r0 - RR; q < r0; ++q) push_row(q);
     for (int q = r0; q < r0 + RR; ++q) {
       push_row(q);
