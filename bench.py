@@ -170,6 +170,18 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- our arm
+def aggregate_ranks(ms_local: float, world: int, steps: int, units_per_step: float, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas (weak scaling): the slowest
+    rank's time (max over ranks, the only collective, outside the data path)
+    and units = world x steps x units_per_step over it. Returns (ms_max, value)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps * units_per_step / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -220,11 +232,7 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         ms32 = timed_steps(lambda: h32.macro_step(M, 1), args.steps)
     barrier()
-    t_local = torch.tensor([ms32], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * args.steps * lu_batch / (ms_max / 1e3)
+    ms_max, value = aggregate_ranks(ms32, world, args.steps, lu_batch, dist, "cuda")
     macro_steps_per_s = args.steps / (ms_max / 1e3)
 
     # --- dominant kernel: the FP32 micro-batch kernel, timed per launch on its stream.
