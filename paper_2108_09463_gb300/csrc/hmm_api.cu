@@ -341,8 +341,7 @@ hmm_status build(HmmHandle* h) {
     if (p.reserved[i] != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
   if (p.model != HMM_FIELD_MODEL && p.model != HMM_FLUX_MODEL)
     return fail(h, HMM_ERR_INVALID_ARG, "model must be 0 (field) or 1 (flux)");
-  if (p.model == HMM_FLUX_MODEL && p.kernel_variant == 2)
-    return fail(h, HMM_ERR_INVALID_ARG, "the flux model runs on the generic kernel");
+
   if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
     return fail(h, HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
   h->dim = p.dim;
@@ -548,10 +547,10 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  std::string why = "the resident kernels need the FP32 form, HeunP, the field model and d = 2 or 3";
+  std::string why = "the resident kernels need the FP32 form, HeunP and d = 2 or 3 (the flux model: d = 2)";
   const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 && p.micro_stepper == HMM_HEUNP &&
-                      p.model == HMM_FIELD_MODEL &&
-                      res2d_make_plan(h->dim, h->boxes.data(), h->P, h->radius, h->interp_k, p.n_terms,
+                      (p.model == HMM_FIELD_MODEL || h->dim == 2) &&
+                      res2d_make_plan(h->dim, h->boxes.data(), h->nb, h->radius, h->interp_k, p.n_terms,
                                       (size_t)optin - 256, &h->plan, &why) &&
                       (int)h->plan.groups.size() <= kQueues;
   if (p.kernel_variant == 2 && !res_ok) return fail(h, HMM_ERR_INVALID_ARG, why.c_str());

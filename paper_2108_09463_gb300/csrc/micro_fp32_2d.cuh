@@ -465,13 +465,22 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       auto fdiff = [](const double* u, int o, int st_) {   // the face difference at face o
         return R == 3 ? (u[o - st_] - u[o + 2 * st_]) + 27.0 * (u[o + st_] - u[o]) : u[o + st_] - u[o];
       };
+      // Flux model (bd.fax = k): the box averages a_f D_k m over the faces along k
+      // instead of H. By summation by parts its state part is sum_xi G(xi) v(xi)
+      // with G = -fcomb(WA) / (24 dx) (order 2: / dx), WA_f = W_f a_f the face
+      // weight times the coefficient: the fourth flux component then holds WA on
+      // the axis k faces (zero on the other axis), and G takes H(W)'s place in the
+      // time loop's average. W_f: face weights along k (after the node weights in
+      // the table) times node weights along the other axis.
+      const int fax = bd.fax;
+      const double* W1f = W1d + N;
       for (int e = tid; e < nxf * Ni; e += nt) {
         const int f = xf0 + e / Ni, j = R + e % Ni;
         const int o = f * N + j;
         const double af = af64[o];
 #pragma unroll
         for (int c = 0; c < 3; ++c) flx[c * cap + o] = af * fdiff(mi64 + c * cap, o, N);
-        flx[3 * cap + o] = af * W1d[j] * fdiff(W1d, f, 1);
+        flx[3 * cap + o] = fax < 0 ? af * W1d[j] * fdiff(W1d, f, 1) : (fax == 0 ? af * W1f[f] * W1d[j] : 0.0);
       }
       for (int e = tid; e < S * nyg; e += nt) {
         const int i = r0 + R + e / nyg, g = yg0 + e % nyg;
@@ -479,26 +488,48 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         const double af = af64[cap + o];
 #pragma unroll
         for (int c = 0; c < 3; ++c) fly[c * cap + o] = af * fdiff(mi64 + c * cap, o, 1);
-        fly[3 * cap + o] = af * W1d[i] * fdiff(W1d, g, 1);
+        fly[3 * cap + o] = fax < 0 ? af * W1d[i] * fdiff(W1d, g, 1) : (fax == 1 ? af * W1d[i] * W1f[g] : 0.0);
       }
       __syncthreads();
       auto fcomb = [](const double* F, int o, int st_) {   // node combination of the fluxes
         return R == 3 ? (F[o - 2 * st_] - F[o + st_]) + 27.0 * (F[o] - F[o - st_]) : F[o] - F[o - st_];
       };
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      const double cf = R == 3 ? 1.0 / (24.0 * bd.dx) : 1.0 / bd.dx;
       for (int e = tid; e < S * Ni; e += nt) {
         const int ii = e / Ni, jj = e - ii * Ni;
         const int idx = (r0 + ii + R) * N + (jj + R);
         double H[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) H[c] = (fcomb(flx + c * cap, idx, N) + fcomb(fly + c * cap, idx, 1)) * cs64;
-        const double W = W1d[r0 + ii + R] * W1d[jj + R];
-        s0 += W * H[0];
-        s1 += W * H[1];
-        s2 += W * H[2];
+        for (int c = 0; c < 3; ++c) H[c] = (fcomb(flx + c * cap, idx, N) + fcomb(fly + c * cap, idx, 1)) * cs64;
+        const double c3 = fcomb(flx + 3 * cap, idx, N) + fcomb(fly + 3 * cap, idx, 1);
+        H[3] = fax < 0 ? c3 * cs64 : -c3 * cf;
+        if (fax < 0) {
+          const double W = W1d[r0 + ii + R] * W1d[jj + R];
+          s0 += W * H[0];
+          s1 += W * H[1];
+          s2 += W * H[2];
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) hiS[(c * d.S + ii) * d.LDI + jj] = (float)H[c];
         hwS[ii * d.LDI + jj] = (float)H[3];
+      }
+      if (fax >= 0) {
+        // the flux of m_init over the faces along k this CTA owns: along the slab's
+        // axis the faces f in [r0 + R, r0 + R + S) (and f = R - 1 in the first slab),
+        // along the other axis the faces R-1 .. N-R-1 of the slab's rows
+        const int fa = fax == 0 ? r0 + R - (r0 == 0 ? 1 : 0) : R - 1;
+        const int fb = fax == 0 ? r0 + R + S : N - R;
+        const int nfa = fb - fa, nother = fax == 0 ? Ni : S;
+        for (int e = tid; e < nfa * nother; e += nt) {
+          const int f = fa + e / nother, u = e % nother;
+          const int o = fax == 0 ? f * N + (R + u) : (r0 + R + u) * N + f;
+          const double WF = fax == 0 ? W1f[f] * W1d[R + u] : W1d[r0 + R + u] * W1f[f];
+          const double* Fl = fax == 0 ? flx : fly;
+          s0 += WF * Fl[o] * cf;
+          s1 += WF * Fl[cap + o] * cf;
+          s2 += WF * Fl[2 * cap + o] * cf;
+        }
       }
       block_sum3(s0, s1, s2, red);
       if (tid == 0) {
@@ -672,10 +703,12 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] += (double)kahA[6 * w + c] - (double)kahA[6 * w + 3 + c];
       if (cs == 1) {
-        const int pt = a.boxes[p.box].p;
-        a.Havg[pt] = acc[0];
-        a.Havg[a.P + pt] = acc[1];
-        a.Havg[2 * a.P + pt] = acc[2];
+        const BoxDesc& ob = a.boxes[p.box];
+        const int pt = ob.p;
+        double* out = ob.fax >= 0 ? a.Fout + (size_t)ob.fax * 3 * a.P : a.Havg;
+        out[pt] = acc[0];
+        out[a.P + pt] = acc[1];
+        out[2 * a.P + pt] = acc[2];
         if (!(isfinite(acc[0]) && isfinite(acc[1]) && isfinite(acc[2]))) atomicOr(a.err, kErrNonFinite);
       } else {
         double* dst = cg::this_cluster().map_shared_rank(csum, 0u) + 4 * rank;
@@ -691,10 +724,12 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         for (int r = 0; r < cs; ++r)
 #pragma unroll
           for (int c = 0; c < 3; ++c) acc[c] += csum[4 * r + c];
-        const int pt = a.boxes[pk[0].box].p;
-        a.Havg[pt] = acc[0];
-        a.Havg[a.P + pt] = acc[1];
-        a.Havg[2 * a.P + pt] = acc[2];
+        const BoxDesc& ob = a.boxes[pk[0].box];
+        const int pt = ob.p;
+        double* out = ob.fax >= 0 ? a.Fout + (size_t)ob.fax * 3 * a.P : a.Havg;
+        out[pt] = acc[0];
+        out[a.P + pt] = acc[1];
+        out[2 * a.P + pt] = acc[2];
         if (!(isfinite(acc[0]) && isfinite(acc[1]) && isfinite(acc[2]))) atomicOr(a.err, kErrNonFinite);
       }
     }

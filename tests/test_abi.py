@@ -98,7 +98,7 @@ def _init(lib, cfg, **over):
     (dict(interp_order=6), "interp_order"), (dict(precision=5), "precision"),
     (dict(micro_steps=0), "micro_steps"), (dict(box_n=5), "box_n"), (dict(box_n=300), "box_n"),
     (dict(eps=-1.0), "eps"), (dict(pts_per_eps=0.0), "pts_per_eps"), (dict(n_terms=9), "n_terms"),
-    (dict(model=2), "model"), (dict(model=1, kernel_variant=2), "generic kernel"),
+    (dict(model=2), "model"),
 ])
 def test_invalid_params_rejected_on_host(lib, over, needle):
     cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=10)

@@ -57,12 +57,18 @@ def _points(cfg, k=4):
     return sorted(set([0, P - 1, P // 2, P // 3]))[:k]
 
 
-@pytest.mark.parametrize("case", sorted(CASES))
+# FP32: the 2D HeunP cases run on the resident kernel (chosen automatically), the
+# others on the generic kernel; "_generic" forces the generic kernel in 2D.
+FP32_CASES = sorted(CASES) + ["2d_generic", "2d_ragged_generic"]
+
+
+@pytest.mark.parametrize("case", FP32_CASES)
 def test_flux_columns_parity_fp32(torch_cuda, case):
     from paper_2108_09463_gb300 import HMM
-    cfg = _cfg(case)
+    variant = 1 if case.endswith("_generic") else 0
+    cfg = _cfg(case.replace("_generic", ""))
     M0 = W.initial_field(cfg)
-    h = HMM(cfg, precision=1)
+    h = HMM(cfg, precision=1, kernel_variant=variant)
     M = torch_cuda.from_numpy(M0).cuda()
     Fg = h.flux_batch(M).cpu().numpy()
     H = h.micro_batch(M).cpu().numpy()
@@ -130,9 +136,10 @@ def test_flux_macro_steps(torch_cuda):
 
 def test_flux_model_validation(torch_cuda):
     from paper_2108_09463_gb300 import HMM, HmmError
-    cfg = _cfg("2d")
     with pytest.raises(HmmError):
-        HMM(cfg, precision=1, kernel_variant=2)     # the resident kernels average H only
+        HMM(_cfg("3d"), precision=1, kernel_variant=2)   # the 3D resident kernel averages H only
+    cfg = _cfg("2d")
+    HMM(cfg, precision=1, kernel_variant=2).close()      # the 2D resident kernel takes the flux
     h = HMM(cfg.replace(model=0), precision=0)
     with pytest.raises(HmmError):
         h.flux_batch(torch_cuda.from_numpy(W.initial_field(cfg)).cuda())
