@@ -547,9 +547,8 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  std::string why = "the resident kernels need the FP32 form, HeunP and d = 2 or 3 (the flux model: d = 2)";
+  std::string why = "the resident kernels need the FP32 form, HeunP and d = 2 or 3";
   const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 && p.micro_stepper == HMM_HEUNP &&
-                      (p.model == HMM_FIELD_MODEL || h->dim == 2) &&
                       res2d_make_plan(h->dim, h->boxes.data(), h->nb, h->radius, h->interp_k, p.n_terms,
                                       (size_t)optin - 256, &h->plan, &why) &&
                       (int)h->plan.groups.size() <= kQueues;

@@ -366,8 +366,18 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         double* F = fl3 + (size_t)k * 4 * cap;
 #pragma unroll
         for (int c = 0; c < 3; ++c) F[c * cap + o] = af * fdiff(mi64 + c * cap, o, st_);
-        const double wd = k == 0 ? W1d[yb] * W1d[xb] * fdiff(W1d, zb, 1)
-                                 : (k == 1 ? W1d[zb] * W1d[xb] * fdiff(W1d, yb, 1) : W1d[zb] * W1d[yb] * fdiff(W1d, xb, 1));
+        // flux model (bd.fax = axis): the fourth component holds W_f a_f on the faces
+        // along that axis (face weights after the node weights in the table), so that
+        // -fcomb of it is the node weight of the flux average (summation by parts)
+        const double* W1f = W1d + N;
+        double wd;
+        if (bd.fax < 0)
+          wd = k == 0 ? W1d[yb] * W1d[xb] * fdiff(W1d, zb, 1)
+                      : (k == 1 ? W1d[zb] * W1d[xb] * fdiff(W1d, yb, 1) : W1d[zb] * W1d[yb] * fdiff(W1d, xb, 1));
+        else if (k != bd.fax)
+          wd = 0.0;
+        else
+          wd = k == 0 ? W1f[zb] * W1d[yb] * W1d[xb] : (k == 1 ? W1d[zb] * W1f[yb] * W1d[xb] : W1d[zb] * W1d[yb] * W1f[xb]);
         F[3 * cap + o] = af * wd;
       }
       __syncthreads();
@@ -375,6 +385,8 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         return R == 3 ? (F[o - 2 * st_] - F[o + st_]) + 27.0 * (F[o] - F[o - st_]) : F[o] - F[o - st_];
       };
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      const int fax = bd.fax;
+      const double cf = R == 3 ? 1.0 / (24.0 * bd.dx) : 1.0 / bd.dx;
       for (int e = tid; e < S * nn; e += nt) {
         const int z = e / nn, yx = e - z * nn, y = yx / Ni, x = yx - y * Ni;
         const size_t idx = bidx(r0 + z + R, y + R, x + R);
@@ -382,8 +394,8 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
           H[c] = (fcomb(fl3 + c * cap, idx, sz) + fcomb(fl3 + (4 + c) * cap, idx, (size_t)N) +
-                  fcomb(fl3 + (8 + c) * cap, idx, 1)) * cs64;
-        const double W = W1d[r0 + z + R] * W1d[y + R] * W1d[x + R];
+                  fcomb(fl3 + (8 + c) * cap, idx, 1)) * (c < 3 || fax < 0 ? cs64 : -cf);
+        const double W = fax < 0 ? W1d[r0 + z + R] * W1d[y + R] * W1d[x + R] : 0.0;
         s0 += W * H[0];
         s1 += W * H[1];
         s2 += W * H[2];
@@ -391,6 +403,29 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) hiS[c * d.Sc * d.PI + io] = (float)H[c];
         hwS[io] = (float)H[3];
+      }
+      if (fax >= 0) {
+        // the flux of m_init over the faces along fax this CTA owns: along z the face
+        // planes [r0 + R, r0 + R + S) (and R - 1 in the first slab), along y or x the
+        // faces R-1 .. N-R-1 of the own planes; the other axes' interior nodes
+        const double* W1f = W1d + N;
+        const int na = fax == 0 ? S + (r0 == 0 ? 1 : 0) : N - 2 * R + 1;
+        const int f0a = fax == 0 ? r0 + R - (r0 == 0 ? 1 : 0) : R - 1;
+        const int nb_ = fax == 0 ? nn : S * Ni;      // (y, x) or (z, other)
+        const double* Fk = fl3 + (size_t)fax * 4 * cap;
+        for (int e = tid; e < na * nb_; e += nt) {
+          const int f = f0a + e / nb_, u = e % nb_;
+          int zb, yb, xb;
+          if (fax == 0) { zb = f; yb = R + u / Ni; xb = R + u % Ni; }
+          else if (fax == 1) { zb = zo + u / Ni; yb = f; xb = R + u % Ni; }
+          else { zb = zo + u / Ni; yb = R + u % Ni; xb = f; }
+          const size_t o = bidx(zb, yb, xb);
+          const double WF = (fax == 0 ? W1f[zb] : W1d[zb]) * (fax == 1 ? W1f[yb] : W1d[yb]) *
+                            (fax == 2 ? W1f[xb] : W1d[xb]);
+          s0 += WF * Fk[o] * cf;
+          s1 += WF * Fk[cap + o] * cf;
+          s2 += WF * Fk[2 * cap + o] * cf;
+        }
       }
       block_sum3(s0, s1, s2, red);
       if (tid == 0) {
@@ -576,9 +611,10 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] += (double)kahA[6 * w + c] - (double)kahA[6 * w + 3 + c];
       if (cs == 1) {
-        a.Havg[bd.p] = acc[0];
-        a.Havg[a.P + bd.p] = acc[1];
-        a.Havg[2 * a.P + bd.p] = acc[2];
+        double* out = bd.fax >= 0 ? a.Fout + (size_t)bd.fax * 3 * a.P : a.Havg;
+        out[bd.p] = acc[0];
+        out[a.P + bd.p] = acc[1];
+        out[2 * a.P + bd.p] = acc[2];
         if (!(isfinite(acc[0]) && isfinite(acc[1]) && isfinite(acc[2]))) atomicOr(a.err, kErrNonFinite);
       } else {
         double* dst = cg::this_cluster().map_shared_rank(csum, 0u) + 4 * rank;
@@ -594,9 +630,10 @@ micro_fp32_3d_kernel(MicroArgs a, ResLaunch L) {
         for (int r = 0; r < cs; ++r)
 #pragma unroll
           for (int c = 0; c < 3; ++c) acc[c] += csum[4 * r + c];
-        a.Havg[bd.p] = acc[0];
-        a.Havg[a.P + bd.p] = acc[1];
-        a.Havg[2 * a.P + bd.p] = acc[2];
+        double* out = bd.fax >= 0 ? a.Fout + (size_t)bd.fax * 3 * a.P : a.Havg;
+        out[bd.p] = acc[0];
+        out[a.P + bd.p] = acc[1];
+        out[2 * a.P + bd.p] = acc[2];
         if (!(isfinite(acc[0]) && isfinite(acc[1]) && isfinite(acc[2]))) atomicOr(a.err, kErrNonFinite);
       }
     }

@@ -57,9 +57,9 @@ def _points(cfg, k=4):
     return sorted(set([0, P - 1, P // 2, P // 3]))[:k]
 
 
-# FP32: the 2D HeunP cases run on the resident kernel (chosen automatically), the
-# others on the generic kernel; "_generic" forces the generic kernel in 2D.
-FP32_CASES = sorted(CASES) + ["2d_generic", "2d_ragged_generic"]
+# FP32: the 2D and 3D HeunP cases run on the resident kernels (chosen automatically),
+# the others on the generic kernel; "_generic" forces the generic kernel.
+FP32_CASES = sorted(CASES) + ["2d_generic", "2d_ragged_generic", "3d_generic"]
 
 
 @pytest.mark.parametrize("case", FP32_CASES)
@@ -137,9 +137,9 @@ def test_flux_macro_steps(torch_cuda):
 def test_flux_model_validation(torch_cuda):
     from paper_2108_09463_gb300 import HMM, HmmError
     with pytest.raises(HmmError):
-        HMM(_cfg("3d"), precision=1, kernel_variant=2)   # the 3D resident kernel averages H only
+        HMM(_cfg("1d"), precision=1, kernel_variant=2)   # no 1D resident kernel
     cfg = _cfg("2d")
-    HMM(cfg, precision=1, kernel_variant=2).close()      # the 2D resident kernel takes the flux
+    HMM(cfg, precision=1, kernel_variant=2).close()      # the resident kernels take the flux
     h = HMM(cfg.replace(model=0), precision=0)
     with pytest.raises(HmmError):
         h.flux_batch(torch_cuda.from_numpy(W.initial_field(cfg)).cuda())
