@@ -92,6 +92,13 @@ hmm_status hmm_dns_reset(void* handle);
  * hmm_dns_step call in ms. Any pointer may be NULL. */
 hmm_status hmm_dns_info(void* handle, double* dt, long long* j, double* last_ms);
 
+/* The work plan of the time-stepping kernel: warp strips along the fast axis,
+ * rows per work item (chunk) and work items. The chunk starts as the longest
+ * that keeps every resident warp busy in one wave; the first time step after the
+ * RK4P start-up autotunes it (times the kernel for a few chunk lengths on the
+ * handle's own grid and keeps the fastest). Any pointer may be NULL. */
+hmm_status hmm_dns_plan(void* handle, int* strips, int* chunk, int* items);
+
 /* One-line description of the last failure on this handle ("" if none);
  * NULL handle: the last hmm_dns_init failure. */
 const char* hmm_dns_last_error(void* handle);

@@ -26,7 +26,7 @@ EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_st
             "hmm_flux_batch", "hmm_last_error", "hmm_destroy")
 # The symbols include/hmm_dns.h declares.
 EXPORTED_DNS = ("hmm_dns_init", "hmm_dns_set_face_table", "hmm_dns_step", "hmm_dns_step_host",
-                "hmm_dns_reset", "hmm_dns_info", "hmm_dns_last_error", "hmm_dns_destroy")
+                "hmm_dns_reset", "hmm_dns_info", "hmm_dns_plan", "hmm_dns_last_error", "hmm_dns_destroy")
 
 
 class HmmCoefTerm(ctypes.Structure):
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_dns_step_host.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_dns_reset.argtypes = [c_void_p]
     lib.hmm_dns_info.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]
+    lib.hmm_dns_plan.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]
     lib.hmm_dns_last_error.argtypes = [c_void_p]
     lib.hmm_dns_last_error.restype = c_char_p
     lib.hmm_dns_destroy.argtypes = [c_void_p]
@@ -378,6 +379,12 @@ class DNS:
         dt, j, ms = c_double(), c_longlong(), c_double()
         self._check(self.lib.hmm_dns_info(self.h, ctypes.byref(dt), ctypes.byref(j), ctypes.byref(ms)))
         return dict(dt=dt.value, j=int(j.value), last_ms=ms.value)
+
+    def plan(self):
+        """The time-stepping kernel's work plan (see hmm_dns_plan)."""
+        st, ch, it = c_int(), c_int(), c_int()
+        self._check(self.lib.hmm_dns_plan(self.h, ctypes.byref(st), ctypes.byref(ch), ctypes.byref(it)))
+        return dict(strips=st.value, chunk=ch.value, items=it.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -55,6 +55,7 @@ struct DnsHandle {
   int* d_err = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_ms = 0;
+  bool tuned = false;             // the work plan has been autotuned
   std::string err;
 };
 
@@ -386,26 +387,76 @@ hmm_status enqueue_rk4_step(DnsHandle* h, double* M) {
   return HMM_OK;
 }
 
-hmm_status enqueue_mpea_step(DnsHandle* h) {
-  Args a = h->base;
+// Arguments of the time-stepping kernel for step j from state cur (the next
+// state goes to the other buffer); returns the kernel mode.
+int mpea_args(const DnsHandle* h, Args& a) {
+  a = h->base;
   const int nxt = 1 - h->cur;
   a.h1 = h->d_hist[(h->j - 1) % 3];
   a.h2 = h->d_hist[(h->j - 2) % 3];
   a.h_out = h->d_hist[h->j % 3];
   a.err = h->d_err;
-  int mode;
   if (h->precision == HMM_FP64_PLAIN) {
     a.m64 = (const double*)h->d_state[h->cur];
     a.m64_out = (double*)h->d_state[nxt];
-    mode = kMpea64;
-  } else {
-    a.ff = (const float2*)h->d_state[h->cur];
-    a.ff_out = (float2*)h->d_state[nxt];
-    mode = kMpeaFF;
+    return kMpea64;
   }
+  a.ff = (const float2*)h->d_state[h->cur];
+  a.ff_out = (float2*)h->d_state[nxt];
+  return kMpeaFF;
+}
+
+hmm_status enqueue_mpea_step(DnsHandle* h) {
+  Args a;
+  const int mode = mpea_args(h, a);
   cudaError_t e = launch_stencil(mode, h, a);
   if (e != cudaSuccess) return cuda_fail(h, e, "dns mpea kernel launch");
-  h->cur = nxt;
+  h->cur = 1 - h->cur;
+  return HMM_OK;
+}
+
+void set_chunk(DnsHandle* h, int chunk) {
+  Args& a = h->base;
+  a.chunk = chunk;
+  a.chunks = (h->n0 + chunk - 1) / chunk;
+  a.items = a.strips * a.chunks;
+}
+
+// Autotuner of the work plan, run once at the first time step of the
+// time-stepping kernel (when the history exists and the state is real): the
+// kernel is timed on this grid for a few chunk lengths (rows per work item) --
+// the one-wave plan, half, twice and four times it, at least 8 rows and at most
+// n0 -- one warm-up and three timed launches each, writing the next state and
+// history slots, which the real step then overwrites. The fastest plan is kept;
+// the six-step graphs are captured after it.
+hmm_status autotune(DnsHandle* h) {
+  h->tuned = true;
+  if (h->d == 1) return HMM_OK;
+  const int c1 = h->base.chunk;
+  std::vector<int> cands;
+  for (int c : {c1, std::max(8, c1 / 2), std::min(h->n0, 2 * c1), std::min(h->n0, 4 * c1)})
+    if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+  int best = c1;
+  float best_ms = 1e30f;
+  for (int c : cands) {
+    set_chunk(h, c);
+    Args a;
+    const int mode = mpea_args(h, a);
+    cudaError_t e = launch_stencil(mode, h, a);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_stencil(mode, h, a);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->ev1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dns autotune");
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  set_chunk(h, best);
+  DNS_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   return HMM_OK;
 }
 
@@ -476,6 +527,7 @@ hmm_status run_steps(DnsHandle* h, double* M_dev, int n_steps) {
       dns_split<<<pw_blocks(G), 256, 0, h->stream>>>(G, h->d_m64, (float2*)h->d_state[h->cur]);
       in_m64 = false;
     }
+    if (!h->tuned) DNS_TRY(autotune(h));
     if (n_steps - s >= 6) {
       DNS_TRY(launch_six(h));
       s += 6;
@@ -646,6 +698,15 @@ hmm_status hmm_dns_step_host(void* handle, double* M_host, int n_steps) {
   DNS_TRY(run_steps(h, h->d_host_io, n_steps));
   DNS_CUDA(h, cudaMemcpyAsync(M_host, h->d_host_io, bytes, cudaMemcpyDeviceToHost, h->stream));
   DNS_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HMM_OK;
+}
+
+hmm_status hmm_dns_plan(void* handle, int* strips, int* chunk, int* items) {
+  DnsHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (strips) *strips = h->base.strips;
+  if (chunk) *chunk = h->base.chunk;
+  if (items) *items = h->base.items;
   return HMM_OK;
 }
 

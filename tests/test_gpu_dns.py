@@ -156,3 +156,24 @@ def test_dns_full_size_sampled(torch_cuda, precision):
         ref = D.patch_run(cfg, M0, c, steps, info["dt"])
         e = float(np.linalg.norm(Mg[:, c[0], c[1]] - ref))
         assert e < TOL[precision], (c, precision, e)
+
+
+def test_dns_plan_autotuned(torch_cuda):
+    """The first MPEA step autotunes the chunk length among the one-wave plan,
+    half, twice and four times it; the results do not depend on the plan."""
+    from paper_2108_09463_gb300 import DNS
+    cfg = _cfg((300, 260), 4)
+    M0 = W.dns_initial(cfg, noise=0.1, seed=4)
+    d = DNS(cfg, precision=1)
+    p0 = d.plan()
+    M = torch_cuda.from_numpy(M0.copy()).cuda()
+    d.step(M, 2)                       # start-up only: no tuning yet
+    assert d.plan() == p0
+    d.step(M, 7)
+    p1 = d.plan()
+    d.close()
+    c1 = p0["chunk"]
+    assert p1["chunk"] in {c1, max(8, c1 // 2), min(300, 2 * c1), min(300, 4 * c1)}
+    assert p1["items"] == p1["strips"] * ((300 + p1["chunk"] - 1) // p1["chunk"])
+    M2, _ = _gpu(torch_cuda, cfg, M0, 9, 1)
+    assert np.abs(M.cpu().numpy() - M2).max() == 0.0
