@@ -28,7 +28,7 @@ step, with the micro problem, kernels, weights and time stepping of
 """
 from __future__ import annotations
 
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, Optional, Sequence
 
 import numpy as np
 

@@ -12,7 +12,6 @@ import pytest
 
 import workloads as W
 from oracle import flux_oracle as F
-from oracle import hmm_oracle as O
 
 pytestmark = pytest.mark.gpu
 
