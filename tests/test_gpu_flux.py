@@ -40,13 +40,16 @@ CASES = {
     "2d_slow_fast": ("c3_2d_uneven", dict(n_macro=(8, 8, 1), eps_field=None, box_n_field=None,
                                           eps=1 / 250, box_n=32, micro_steps=30, precision=0)),
     "3d": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=16, mu_over_eps=0.9, micro_steps=20, precision=0)),
+    "2d_order2": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30, stencil_order=2)),
+    # uneven boxes (N = 32..96 by eq. G15's eps field on an 8 x 8 grid): packs and clusters
+    "2d_uneven": ("c3_2d_uneven", dict(n_macro=(8, 8, 1), micro_steps=12, precision=0)),
 }
 
 
 def _cfg(case):
     name, over = CASES[case]
     cfg = W.config(name, **over).replace(model=1)
-    if name == "c3_2d_uneven":
+    if name == "c3_2d_uneven" and "eps_field" in over:
         cfg = cfg.replace(eps_field=None, box_n_field=None)
     return cfg
 
