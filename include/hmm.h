@@ -235,6 +235,16 @@ hmm_status hmm_macro_dt(void* handle, double* dt_macro);
 hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const double* M_dev, double* Havg_dev,
                                    void* cuda_stream);
 
+/* The resident-plan autotuner's record for this handle: one line per box size
+ * N of the batch that more than one resident-kernel instance can hold, with the
+ * device time of each candidate (canvas size or box stride, CTAs per cluster)
+ * on a sample of that size's boxes and the index of the one kept. hmm_init runs
+ * the autotuner when it picks the resident 2D kernel; "" when there was
+ * nothing to choose or another kernel runs. The string is owned by the handle
+ * and valid until hmm_destroy. NULL handle: "". This entry point is an addition
+ * of this library; the paper has no counterpart. */
+const char* hmm_plan_report(void* handle);
+
 /* One-line description of the last failure on this handle ("" if none). Valid
  * until the next call on the handle. NULL handle: the last hmm_init failure. */
 const char* hmm_last_error(void* handle);

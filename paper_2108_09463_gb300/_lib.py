@@ -23,7 +23,7 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
             "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
             "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
-            "hmm_flux_batch", "hmm_last_error", "hmm_destroy")
+            "hmm_flux_batch", "hmm_plan_report", "hmm_last_error", "hmm_destroy")
 # The symbols include/hmm_dns.h declares.
 EXPORTED_DNS = ("hmm_dns_init", "hmm_dns_set_face_table", "hmm_dns_step", "hmm_dns_step_host",
                 "hmm_dns_reset", "hmm_dns_info", "hmm_dns_plan", "hmm_dns_last_error", "hmm_dns_destroy")
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_micro_batch_noalloc.argtypes = [POINTER(HmmParams), c_void_p, c_void_p, c_void_p]
     lib.hmm_last_error.argtypes = [c_void_p]
     lib.hmm_last_error.restype = c_char_p
+    lib.hmm_plan_report.argtypes = [c_void_p]
+    lib.hmm_plan_report.restype = c_char_p
     lib.hmm_destroy.argtypes = [c_void_p]
     lib.hmm_destroy.restype = None
     lib.hmm_dns_init.argtypes = [POINTER(HmmDnsParams), c_void_p, POINTER(c_void_p)]
@@ -99,7 +101,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_dns_destroy.argtypes = [c_void_p]
     lib.hmm_dns_destroy.restype = None
     for name in EXPORTED + EXPORTED_DNS:
-        if name not in ("hmm_last_error", "hmm_destroy", "hmm_dns_last_error", "hmm_dns_destroy"):
+        if name not in ("hmm_last_error", "hmm_plan_report", "hmm_destroy", "hmm_dns_last_error",
+                        "hmm_dns_destroy"):
             getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -287,6 +290,10 @@ class HMM:
         self._check(self.lib.hmm_box_info(self.h, c_void_p(dt.ctypes.data), c_void_p(mu.ctypes.data),
                                           c_void_p(dx.ctypes.data), c_void_p(n.ctypes.data)))
         return dict(dt=dt, mu=mu, dx=dx, N=n)
+
+    def plan_report(self):
+        """The resident-plan autotuner's timings (hmm_plan_report), one line per box size."""
+        return self.lib.hmm_plan_report(self.h).decode()
 
     def macro_dt(self):
         v = c_double()

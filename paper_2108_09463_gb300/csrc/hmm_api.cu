@@ -267,6 +267,7 @@ struct HmmHandle {
   // device
   BoxDesc* d_boxes = nullptr;
   int nb = 0;                      // boxes: P (field model) or d P (flux model)
+  std::string plan_report;         // the resident-plan autotuner's timings
   double* d_F = nullptr;           // flux model: F_avg, d x 3 x P
   double* d_W64 = nullptr;
   float* d_W32 = nullptr;
@@ -333,6 +334,138 @@ void free_all(HmmHandle* h) {
 }
 
 int max_n_for_dim(int d) { return d == 1 ? 1024 : (d == 2 ? 256 : 64); }
+
+// Autotuner of the resident 2D plan. For every box size of the batch with more
+// than one kernel instance that holds it (compile-time canvases, the box-stride
+// instance, cluster sizes), the micro kernel is timed for each candidate on a
+// sample of that size's boxes (up to 8 per SM): a constant macro field, the
+// first min(M, 32) micro steps, one warm-up and two timed launches; the fastest
+// candidate is kept and the real plan is rebuilt with it. The results are kept
+// as text (hmm_plan_report).
+hmm_status tune_resident_plan(HmmHandle* h) {
+  const int R = h->radius, k = h->interp_k, nt = h->p.n_terms;
+  const size_t smem = h->plan.smem;
+  std::map<int, std::pair<int, int>> pick;
+  std::string report;
+  double* d_M = nullptr;
+  double* d_out = nullptr;
+  BoxDesc* d_sb = nullptr;
+  int2* d_it = nullptr;
+  char* d_ar = nullptr;
+  size_t ar_bytes = 0;
+  auto release = [&]() {
+    void* ptrs[] = {d_M, d_out, d_sb, d_it, d_ar};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+  };
+  auto tune = [&]() -> hmm_status {
+    const size_t f3 = sizeof(double) * 3 * (size_t)h->P;
+    HMM_CUDA(h, cudaMalloc(&d_M, f3));
+    HMM_CUDA(h, cudaMalloc(&d_out, f3 * h->dim));
+    {
+      std::vector<double> mz(3 * (size_t)h->P, 0.0);
+      for (int q = 0; q < h->P; ++q) mz[2 * (size_t)h->P + q] = 1.0;   // M = e_z
+      HMM_CUDA(h, cudaMemcpy(d_M, mz.data(), f3, cudaMemcpyHostToDevice));
+    }
+    const int cap_sample = 8 * h->num_sms;
+    HMM_CUDA(h, cudaMalloc(&d_sb, sizeof(BoxDesc) * cap_sample));
+    HMM_CUDA(h, cudaMalloc(&d_it, sizeof(int2) * cap_sample));
+    int lo = 0;
+    while (lo < h->nb) {
+      const int N = h->boxes[lo].N;
+      int hi = lo;
+      while (hi < h->nb && h->boxes[hi].N == N) ++hi;
+      const int count = hi - lo;
+      const auto cand = res2d_candidates(N, R, k, nt, smem);
+      lo = hi;
+      if (cand.size() < 2) continue;
+      const int ns = std::min(count, cap_sample);
+      HMM_CUDA(h, cudaMemcpy(d_sb, h->boxes.data() + (hi - count), sizeof(BoxDesc) * ns, cudaMemcpyHostToDevice));
+      float best_ms = 1e30f;
+      int best = 0;
+      std::string line = "N=" + std::to_string(N) + ":";
+      for (size_t c = 0; c < cand.size(); ++c) {
+        std::map<int, std::pair<int, int>> one{{N, cand[c]}};
+        Res2dPlan pl;
+        std::string why;
+        if (!res2d_make_plan(h->dim, h->boxes.data() + (hi - count), ns, R, k, nt, smem, &pl, &why, &one)) continue;
+        if ((int)pl.groups.size() > kQueues) continue;
+        if (res2d_prepare(R, &pl, h->num_sms) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        const size_t need = h->slot_bytes * (size_t)res2d_max_grid(pl);
+        if (need > ar_bytes) {
+          if (d_ar) cudaFree(d_ar);
+          d_ar = nullptr;
+          HMM_CUDA(h, cudaMalloc(&d_ar, need));
+          ar_bytes = need;
+        }
+        HMM_CUDA(h, cudaMemcpy(d_it, pl.items.data(), sizeof(int2) * pl.items.size(), cudaMemcpyHostToDevice));
+        MicroArgs a = h->args;
+        a.boxes = d_sb;
+        a.n_boxes = ns;
+        a.M = d_M;
+        a.Havg = d_out;
+        a.Fout = d_out;
+        a.msteps = std::min(h->args.msteps, 32);
+        a.arena = d_ar;
+        float ms = 0;
+        for (int r = 0; r < 3; ++r) {
+          HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int) * kQueues, h->stream));
+          if (r == 1) HMM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+          HMM_CUDA(h, res2d_launch(a, R, pl, d_it, h->d_queue, h->stream));
+        }
+        HMM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+        HMM_CUDA(h, cudaEventSynchronize(h->ev1));
+        HMM_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        char buf[96];
+        snprintf(buf, sizeof buf, " %s%d x%d %.3f ms", res2d_variant_canvas(cand[c].first) ? "canvas " : "stride ",
+                 res2d_variant_canvas(cand[c].first), cand[c].second, ms / 2);
+        line += buf;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = (int)c;
+        }
+      }
+      if (best_ms < 1e30f) {
+        pick[N] = cand[best];
+        line += " -> " + std::to_string(best + 1) + "\n";
+        report += line;
+      }
+    }
+    HMM_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+    if (pick.empty()) return HMM_OK;
+    // the real plan with the tuned instances
+    Res2dPlan pl;
+    std::string why;
+    if (!res2d_make_plan(h->dim, h->boxes.data(), h->nb, R, k, nt, smem, &pl, &why, &pick) ||
+        (int)pl.groups.size() > kQueues || res2d_prepare(R, &pl, h->num_sms) != cudaSuccess) {
+      cudaGetLastError();
+      return HMM_OK;                // keep the heuristic plan
+    }
+    const int grid = res2d_max_grid(pl);
+    if (grid > h->grid) {
+      char* ar = nullptr;
+      HMM_CUDA(h, cudaMalloc(&ar, h->slot_bytes * (size_t)grid));
+      cudaFree(h->d_arena);
+      h->d_arena = ar;
+      h->args.arena = ar;
+      h->grid = grid;
+    }
+    int2* it = nullptr;
+    HMM_CUDA(h, cudaMalloc(&it, sizeof(int2) * pl.items.size()));
+    HMM_CUDA(h, cudaMemcpy(it, pl.items.data(), sizeof(int2) * pl.items.size(), cudaMemcpyHostToDevice));
+    cudaFree(h->d_items);
+    h->d_items = it;
+    h->plan = pl;
+    return HMM_OK;
+  };
+  const hmm_status st = tune();
+  release();
+  h->plan_report = report;
+  return st;
+}
 
 hmm_status build(HmmHandle* h) {
   hmm_params& p = h->p;
@@ -613,6 +746,10 @@ hmm_status build(HmmHandle* h) {
   a.arena = h->d_arena;
   a.slot_bytes = h->slot_bytes;
   a.nmax = h->nmax;
+  if (h->res2d && h->dim == 2) {
+    const hmm_status st = tune_resident_plan(h);
+    if (st != HMM_OK) return st;
+  }
   return HMM_OK;
 }
 
@@ -951,6 +1088,11 @@ hmm_status hmm_macro_dt(void* handle, double* dt_macro) {
   if (!dt_macro) return fail(h, HMM_ERR_INVALID_ARG, "null pointer");
   *dt_macro = h->dt_macro;
   return HMM_OK;
+}
+
+const char* hmm_plan_report(void* handle) {
+  HmmHandle* h = as_handle(handle);
+  return h ? h->plan_report.c_str() : "";
 }
 
 const char* hmm_last_error(void* handle) {

@@ -1,5 +1,9 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -102,8 +106,15 @@ struct Res2dPlan {
   int dim = 2;      // 2: micro_fp32_2d_kernel instances, 3: micro_fp32_3d_kernel instances
 };
 // False (with the reason) when some box fits no cluster of the portable size.
+// pick: per box size N, the (instance, cluster size) to use instead of the
+// heuristic's choice (the autotuner's result), or NULL.
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
-                     Res2dPlan* plan, std::string* why);
+                     Res2dPlan* plan, std::string* why,
+                     const std::map<int, std::pair<int, int>>* pick = nullptr);
+// The (instance, cluster size) pairs that hold a 2D box of N nodes, the
+// heuristic's choice first; the canvas size of an instance (0: box stride).
+std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes);
+int res2d_variant_canvas(int vi);
 cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms);
 int res2d_max_grid(const Res2dPlan& plan);
 size_t res2d_slot_bytes(int nmax);

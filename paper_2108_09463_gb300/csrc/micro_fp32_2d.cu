@@ -7,6 +7,9 @@
 
 #include "micro_fp32_3d.cuh"
 
+#include <map>
+#include <utility>
+
 namespace hmm {
 
 size_t res2d_slot_bytes(int nmax) { return (res2d_arena_doubles(nmax) * 8 + 255) & ~(size_t)255; }
@@ -74,7 +77,8 @@ bool cluster_ok(int cs, int Sa, int Ni, int R) {
 bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out) {
   const auto& V = variants(2);
   const int Ni = N - 2 * R;
-  for (int i = 0; i < (int)V.size(); ++i) {
+  int canvases = 0;
+  for (int i = 0; i < (int)V.size() && canvases < 3; ++i) {
     const ResVariant& v = V[i];
     if (v.R != R || v.NC == 0 || v.NC < N) continue;
     const int Sa = (Ni + v.cs - 1) / v.cs;
@@ -101,14 +105,63 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
 
 }  // namespace
 
+std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes) {
+  // the (instance, cluster size) pairs worth timing for a 2D box of N nodes: the
+  // heuristic's own choice first, the three smallest canvases that hold the box (a
+  // larger canvas only adds idle threads and shared memory) and the box-stride
+  // instance with the two smallest cluster sizes that fit
+  const size_t budget = smem_bytes / sizeof(float);
+  const auto& V = variants(2);
+  const int Ni = N - 2 * R;
+  std::vector<std::pair<int, int>> out;
+  int vi = -1, cs = 0;
+  if (choose(N, R, interp_k, n_terms, budget, &vi, &cs)) out.emplace_back(vi, cs);
+  int canvases = 0;
+  for (int i = 0; i < (int)V.size() && canvases < 3; ++i) {
+    const ResVariant& v = V[i];
+    if (v.R != R || v.NC == 0 || v.NC < N) continue;
+    const int Sa = (Ni + v.cs - 1) / v.cs;
+    if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
+    if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
+    ++canvases;
+    if (std::find(out.begin(), out.end(), std::make_pair(i, v.cs)) == out.end()) out.emplace_back(i, v.cs);
+  }
+  for (int i = 0; i < (int)V.size(); ++i) {
+    const ResVariant& v = V[i];
+    if (v.R != R || v.NC != 0) continue;
+    int found = 0;
+    for (int c = 1; c <= kResMaxCluster && found < 2; ++c) {
+      const int Sa = (Ni + c - 1) / c;
+      if (!cluster_ok(c, Sa, Ni, R) || !slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
+      ++found;
+      if (std::find(out.begin(), out.end(), std::make_pair(i, c)) == out.end()) out.emplace_back(i, c);
+    }
+  }
+  return out;
+}
+
+int res2d_variant_canvas(int vi) { return variants(2)[vi].NC; }
+
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
-                     Res2dPlan* plan, std::string* why) {
+                     Res2dPlan* plan, std::string* why, const std::map<int, std::pair<int, int>>* pick) {
   const size_t budget = smem_bytes / sizeof(float);
   const auto& V = variants(2);
   plan->items.clear();
   plan->groups.clear();
   plan->smem = smem_bytes;
   plan->dim = dim;
+  // the instance and cluster size of a box of N nodes: the tuned pick when there is one
+  auto choose_for = [&](int N, int* vi, int* cs) {
+    if (pick) {
+      const auto it = pick->find(N);
+      if (it != pick->end()) {
+        *vi = it->second.first;
+        *cs = it->second.second;
+        return true;
+      }
+    }
+    return choose(N, R, interp_k, n_terms, budget, vi, cs);
+  };
   int i = 0;
   while (i < n) {
     int vi = -1, cs = 0;
@@ -124,7 +177,7 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
       ++i;
       continue;
     }
-    if (!choose(boxes[i].N, R, interp_k, n_terms, budget, &vi, &cs)) {
+    if (!choose_for(boxes[i].N, &vi, &cs)) {
       *why = "a box of N = " + std::to_string(boxes[i].N) + " fits no cluster of at most " +
              std::to_string(kResMaxCluster) + " CTAs";
       return false;
@@ -138,7 +191,7 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
       while (i + k < n && k < kResMaxPack) {
         const int N = boxes[i + k].N, Ni = N - 2 * R;
         int vj = -1, csj = 0;
-        if (!choose(N, R, interp_k, n_terms, budget, &vj, &csj) || vj != vi || csj != 1) break;
+        if (!choose_for(N, &vj, &csj) || vj != vi || csj != 1) break;
         const ResDims dq = geom(V[vi], N, Ni);
         const size_t f = res_offsets(dq).total;
         const int w = (res_tiles(Ni, dq.CPp) + 31) / 32;

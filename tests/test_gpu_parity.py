@@ -270,6 +270,43 @@ def test_resident_2d_kernel_full_size_sampled(torch_cuda):
     assert rel_err(Hg[:, pts], Hr) < TOL[1]
 
 
+def _parse_plan_report(text):
+    """{N: (number of candidates timed, index kept)} from hmm_plan_report's lines."""
+    out = {}
+    for line in text.strip().splitlines():
+        head, rest = line.split(":", 1)
+        timed, kept = rest.rsplit("->", 1)
+        out[int(head[2:])] = (timed.count(" ms"), int(kept))
+    return out
+
+
+@pytest.mark.parametrize("name,over", [("c3_2d_uneven", dict(n_macro=(8, 8, 1), micro_steps=12)),
+                                        ("c2_2d", {})], ids=["uneven_small", "c2_full"])
+def test_resident_plan_autotuner(torch_cuda, name, over):
+    """hmm_init times every resident-kernel instance that holds a box size on a
+    sample of its boxes and keeps the fastest; the tuned plan keeps parity."""
+    from paper_2108_09463_gb300 import HMM
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    h = HMM(cfg, precision=1, kernel_variant=2)
+    rep = _parse_plan_report(h.plan_report())
+    info = h.box_info()
+    Hg = h.micro_batch(torch_cuda.from_numpy(M0).cuda()).cpu().numpy()
+    h.close()
+    assert rep, "no box size had two candidates"
+    sizes = set(int(v) for v in info["N"])
+    for N, (timed, kept) in rep.items():
+        assert N in sizes and timed >= 2 and 1 <= kept <= timed, (N, timed, kept)
+    N = info["N"]
+    pts = sorted(set([int(np.argmin(N)), int(np.argmax(N)), cfg.n_points - 1] +
+                     list(np.random.default_rng(5).choice(cfg.n_points, 4, replace=False))))
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1]
+    h64 = HMM(cfg.replace(n_macro=(6, 6, 1), eps_field=None, box_n_field=None), precision=0)
+    assert h64.plan_report() == ""
+    h64.close()
+
+
 FULL = [("c2_2d", 0), ("c2_2d", 1), ("c3_2d_uneven", 1)]
 
 
