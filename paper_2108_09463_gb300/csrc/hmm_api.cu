@@ -455,7 +455,11 @@ hmm_status tune_resident_plan(HmmHandle* h) {
     }
     int2* it = nullptr;
     HMM_CUDA(h, cudaMalloc(&it, sizeof(int2) * pl.items.size()));
-    HMM_CUDA(h, cudaMemcpy(it, pl.items.data(), sizeof(int2) * pl.items.size(), cudaMemcpyHostToDevice));
+    const cudaError_t e = cudaMemcpy(it, pl.items.data(), sizeof(int2) * pl.items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(it);
+      return cuda_fail(h, e, "cudaMemcpy(tuned work items)");
+    }
     cudaFree(h->d_items);
     h->d_items = it;
     h->plan = pl;
