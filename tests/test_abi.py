@@ -107,6 +107,12 @@ def test_invalid_params_rejected_on_host(lib, over, needle):
     assert needle in msg
 
 
+def test_single_micro_step_rejected_on_host(lib):
+    """M = 1: both time nodes are end points of K0's support, so every weight vanishes."""
+    st, msg = _init(lib, W.config("c2_2d", n_macro=(6, 6, 1), box_n=24, micro_steps=1))
+    assert st == 1 and "time weights" in msg, (st, msg)
+
+
 def test_averaging_box_must_avoid_ring(lib):
     cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=20, micro_steps=10)  # mu = 0.8 mu' reaches the ring
     st, msg = _init(lib, cfg)

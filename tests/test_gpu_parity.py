@@ -96,6 +96,37 @@ def test_small_parity(torch_cuda, case, precision):
         assert abs(info["mu"][p] / geo["mu"] - 1) < 1e-14
 
 
+# Edge sizes: the smallest boxes (one interior node pair per axis, N = 2r + 2, with the
+# averaging box [-mu, mu] shrunk inside the interior), the fewest micro steps that give
+# a non-zero time average (M = 2: w_1 = 1), and the largest box per dimension that
+# hmm_init accepts (N = 1024 / 256 / 64 for d = 1 / 2 / 3).
+EDGE = {
+    "2d_min_box_order4": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=8, mu_over_eps=0.15, micro_steps=30)),
+    "2d_min_box_order2": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=4, stencil_order=2, mu_over_eps=0.15,
+                                        micro_steps=30)),
+    "2d_two_micro_steps": ("c2_2d", dict(n_macro=(6, 6, 1), box_n=24, micro_steps=2)),
+    "1d_max_box": ("c1_1d", dict(n_macro=(8, 1, 1), box_n=1024, micro_steps=20)),
+    "2d_max_box": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=256, micro_steps=8)),
+    "3d_max_box": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=64, micro_steps=4)),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(EDGE))
+def test_edge_sizes_parity(torch_cuda, case, precision):
+    name, over = EDGE[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, precision)
+    assert np.all(np.isfinite(Hg))
+    P = cfg.n_points
+    pts = sorted(set([0, P // 2, P - 1]))
+    _, Hr = reference(cfg, M0, precision, points=pts)
+    e = rel_err(Hg[:, pts], Hr)
+    assert e < TOL[precision], (case, precision, e)
+    assert info["N"][0] == O.box_geometry(cfg, 0)["N"]
+
+
 # The RK4P micro stepper (Section 3.1) on the generic kernels, both precisions.
 RK4P = {
     "1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=60, micro_stepper=1)),
@@ -215,6 +246,8 @@ CLUSTER = {
     "canvas_128": ("c5_sweep", dict(n_macro=(5, 5, 1), box_n=128, micro_steps=20)),
     "box_strides_140": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=140, micro_steps=20)),
     "box_strides_order2_101": ("c2_2d", dict(n_macro=(5, 6, 1), box_n=101, micro_steps=24, stencil_order=2)),
+    # the largest box the resident kernel holds: box strides over a cluster of 8 CTAs
+    "box_strides_160_cluster8": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=160, micro_steps=12)),
 }
 
 
