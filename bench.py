@@ -225,6 +225,7 @@ def run_ours(args, rank, world, local_rank):
     # --- FP32 batched form: full macro steps (RK4P start-up inside warm-up, then MPEA).
     h32 = HMM(cfg, precision=1)
     lu_batch, _ = h32.stats()
+    plan = h32.plan_report().strip()   # the resident-plan autotuner's timings at init
     M = torch.from_numpy(M0).cuda()
     for _ in range(args.warmup):
         h32.macro_step(M, 1)
@@ -337,6 +338,7 @@ def run_ours(args, rank, world, local_rank):
             "fp32_vs_fp64_rel_err": rel,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": 3 * args.steps,
+            "plan_autotuner": plan,
             "dns": dns,
         }
         print(json.dumps(line), flush=True)
