@@ -43,6 +43,10 @@ CASES = {
     "2d_order2": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30, stencil_order=2)),
     # uneven boxes (N = 32..96 by eq. G15's eps field on an 8 x 8 grid): packs and clusters
     "2d_uneven": ("c3_2d_uneven", dict(n_macro=(8, 8, 1), micro_steps=12, precision=0)),
+    # edge sizes: the smallest order-4 box (N = 2r + 2, three weighted faces per axis) and
+    # the fewest micro steps with a non-zero time average (M = 2)
+    "2d_min_box": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=8, mu_over_eps=0.15, micro_steps=20)),
+    "2d_two_micro_steps": ("c2_2d", dict(n_macro=(6, 6, 1), box_n=24, micro_steps=2)),
 }
 
 
