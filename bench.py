@@ -28,6 +28,7 @@ import multiprocessing as mp
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -39,8 +40,9 @@ WORKLOAD = "c2_2d"
 WORKLOAD_DESC = ("2D HMM, 128^2 periodic macro grid, 16384 micro boxes of 64^2 nodes "
                  "(8 per eps, eps=1/200), 400 HeunP micro steps, 4th-order stencil, "
                  "a=1+0.5sin(2pi y1)sin(2pi y2), alpha=0.05, alpha_micro=1.2")
-FLOPS_PER_LU_2D = 255.0     # algorithmic FP32 flops per lattice update, 2D order 4 (count in the design doc)
-BYTES_PER_LU_FP32 = 24.0    # streaming-model bytes per lattice update
+FLOPS_PER_LU_2D = 255.0     # algorithmic FP32 flops per lattice update, 2D order 4: stencil 120,
+                            # m = m_init + v 6, right-hand side 48, stage 1 18, stage 2 63
+BYTES_PER_LU_FP32 = 24.0    # streaming-model bytes per lattice update: 3-component FP32 state read and written
 FP32_LANES_PER_SM = 128
 
 
@@ -123,7 +125,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples: HMM_BENCH_CLOCKS_DIR if set, else the system's temporary directory
+        out_dir = os.environ.get("HMM_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -419,7 +423,7 @@ def run_micro_only(args, local_rank):
 
 # ---------------------------------------------------------------- direct simulation
 DNS_WORKLOAD = "dns_quasi2d"
-# Bytes one time step must move per grid point (DESIGN.md): state read and write,
+# Bytes one time step must move per grid point: state read and write,
 # two history reads and one write, and the two face coefficients. float-float
 # form: 24 + 24 + 24 + 12 + 8 = 92; FP64: 24 + 24 + 48 + 24 + 16 = 136. (Without
 # the coefficient reads, which a separable coefficient could avoid, 84 and 120.)

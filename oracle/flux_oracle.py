@@ -20,7 +20,7 @@ step, with the micro problem, kernels, weights and time stepping of
   at the true positions; the micro time step of the field model);
 * the average of the face flux a_f D_s m along axis k over that axis's faces,
   with the spatial kernel evaluated at the face positions (trapezoid weights,
-  normalised to sum 1 like the node weights, reading G2);
+  normalised to sum 1 like the node weights: the paper fixes no quadrature);
 * the macro divergence (div F)_i = sum_k D_k F_k by the staggered difference of
   the same order as the interpolation (reading: order 4 for Q_[4], order 2 for
   Q_[2]), periodic;

@@ -24,8 +24,8 @@ methods for the Landau-Lifshitz equation", step by step and in FP64:
 * the field-model macro step (Section 2.2, eq. macro_disc) by MPEA
   (Section 3.1, eqs. h_term, h_mpea, mpe_update) with an RK4P start-up.
 
-Readings of places where the paper is silent or garbled are listed in
-DESIGN.md ("Readings of the paper") and cited inline as "reading Gn".
+Where the paper is silent or garbled, the reading taken is stated where it is
+used and marked "a reading".
 Every function here is pinned by the `-m "not gpu"` tests in tests/test_oracle_*.py.
 """
 from __future__ import annotations
@@ -50,7 +50,7 @@ def kernel_coefficients(p: int, q: int) -> List[Fraction]:
 
     K vanishes with its first q derivatives at x = +-1, so K is in C_c^q([-1,1])
     and K^(q+1) is of bounded variation; the c_k are fixed by the p+1 moment
-    conditions int K x^r dx = delta_{r0}, r = 0..p (reading G1: the paper gives
+    conditions int K x^r dx = delta_{r0}, r = 0..p (a reading: the paper gives
     only the kernel space, not a formula). Solved exactly in rationals.
     """
     def base_moment(n: int) -> Fraction:
@@ -133,7 +133,8 @@ def space_weights(N: int, dx: float, mu: float, p: int, q: int, dtype=np.float64
     """Discrete 1D weights of K_mu at the micro nodes xi_j (eq. upscaling).
 
     Trapezoid rule: W_j proportional to dx*K_mu(xi_j) = (dx/mu) K(xi_j/mu), then
-    normalised to sum exactly 1 (reading G2). xi_j = (j - (N-1)/2) dx (reading G6).
+    normalised to sum exactly 1 (a reading: the paper fixes no quadrature).
+    xi_j = (j - (N-1)/2) dx: the box centred on its macro point.
     """
     xi = (np.arange(N, dtype=dtype) - dtype(N - 1) / 2) * dtype(dx)
     W = kernel_eval(xi / dtype(mu), p, q, dtype)
@@ -143,7 +144,8 @@ def space_weights(N: int, dx: float, mu: float, p: int, q: int, dtype=np.float64
 def time_weights(M: int, p: int, q: int, dtype=np.float64) -> np.ndarray:
     """Discrete weights w_n, n = 0..M, of K0_eta at t_n = n*dt, eta = M*dt.
 
-    Trapezoid rule, normalised to sum exactly 1 (reading G2). w_0 = w_M = 0.
+    Trapezoid rule, normalised to sum exactly 1 (a reading: the paper fixes no
+    quadrature). w_0 = w_M = 0.
     """
     t = np.arange(M + 1, dtype=dtype) / dtype(M)
     w = kernel0_eval(t, p, q, dtype)
@@ -210,8 +212,8 @@ def coef_upper_bound(cfg) -> float:
 
 
 def micro_dt(cfg, dx: float, a_max: Optional[float] = None) -> float:
-    """Micro time step dt = safety * s_max(alpha_micro) / omega_max (reading G4), s_max
-    the stability limit of the micro stepper (HeunP or RK4P).
+    """Micro time step dt = safety * s_max(alpha_micro) / omega_max (a reading: the
+    paper states only dt <= C_stab dx^2, eq. Cstab), s_max the stability limit of the micro stepper (HeunP or RK4P).
 
     omega_max = a_max * d * lambda_s / dx^2 bounds the spectral radius of
     -div(a grad) for the staggered stencil; a_max = c0 + sum |amp|.
@@ -227,7 +229,8 @@ MACRO_DT_CONSTANT = 0.06
 
 
 def macro_dt(cfg) -> float:
-    """Macro time step: cfg.dt_macro, or 0.06 * DX^2 / (d * a_max) (reading G9)."""
+    """Macro time step: cfg.dt_macro, or 0.06 * DX^2 / (d * a_max) (a reading: the paper
+    prints no macro step for these problems)."""
     if cfg.dt_macro > 0:
         return cfg.dt_macro
     DX = min(cfg.L / n for n in list(cfg.n_macro)[: cfg.dim])
@@ -270,7 +273,8 @@ def box_geometry(cfg, p: int) -> Dict:
 
 
 def node_offsets(N: int, dx: float, dtype=np.float64) -> np.ndarray:
-    """Micro node coordinates xi_j = (j - (N-1)/2) dx, j = 0..N-1 (reading G6)."""
+    """Micro node coordinates xi_j = (j - (N-1)/2) dx, j = 0..N-1 (the box centred on
+    its macro point)."""
     return (np.arange(N, dtype=dtype) - dtype(N - 1) / 2) * dtype(dx)
 
 
@@ -478,15 +482,17 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
     """One batch of micro problems with a common grid; returns H_avg (B, 3).
 
     m_init: (B, 3, N, ..., N). The micro problem (eq. micro) is stepped by HeunP
-    (Section 3.1): k1 = f(m^n), k2 = f(m^n + dt k1) (reading G18: the standard
+    (Section 3.1): k1 = f(m^n), k2 = f(m^n + dt k1) (a reading: the standard
     Heun second stage, the one for which the stated update is second order),
     m~ = m^n + dt/2 (k1 + k2), m^{n+1} = m~/|m~|; with stepper = 1 by RK4P
     (Section 3.1): k1 = f(m^n), k2 = f(m^n + dt/2 k1), k3 = f(m^n + dt/2 k2),
     k4 = f(m^n + dt k3), m~ = m^n + dt/6 (k1 + 2 k2 + 2 k3 + k4), m^{n+1} =
-    m~/|m~| (reading G10 for the third stage). Only interior nodes move;
+    m~/|m~| (the third stage read as above, where the printed stage repeats
+    k_2). Only interior nodes move;
     ring nodes keep m_init (Dirichlet on m - m_init, Section 4.2).
     The average (eq. upscaling) is sum_n w_n sum_xi W(xi) H(m^n)(xi), with
-    H(m^n) the stage-1 field of step n (reading G8); w_0 = w_M = 0.
+    H(m^n) the stage-1 field of step n (a reading: the paper does not say which
+    stage's field enters); w_0 = w_M = 0.
     W is the (N-2r)^d tensor of interior spatial weights.
 
     With ``flux = (k, Wf)`` the averaged quantity is instead the flux a^eps D_s m
@@ -606,7 +612,7 @@ def midpoint_update(M: np.ndarray, h: np.ndarray, dt: float) -> np.ndarray:
     """Solve (M' - M)/dt = -(M + M')/2 x h for M' per point (eq. mpe_update).
 
     Rearranged: M' + (dt/2) M' x h = M - (dt/2) M x h, a 3x3 linear system per
-    point, solved directly (reading G11: the signs of eq. mpe_update and
+    point, solved directly (a reading: the signs of eq. mpe_update and
     eq. imp_update, not of eq. imp_sys).
     """
     P = M.shape[1]
@@ -627,9 +633,10 @@ class MacroStepper:
     """Field-model HMM macro stepper (eq. macro_disc), MPEA with RK4P start-up.
 
     ``havg(M)`` returns H_avg(x_i; M) for all macro points (default: the
-    oracle's micro_batch). Steps j = 0, 1 use RK4P (Section 3.1, reading G10
-    for the third stage) whose stage states are normalised before their micro
-    solves (reading G13); from j = 2 on MPEA: h^{j+1/2} = 23/12 h^j - 16/12 h^{j-1}
+    oracle's micro_batch). Steps j = 0, 1 use RK4P (Section 3.1; the third stage
+    read as f(M + dt/2 k2) where the printed stage repeats k_2) whose stage states
+    are normalised before their micro solves (a reading: assumption A3 for the
+    micro initial data); from j = 2 on MPEA: h^{j+1/2} = 23/12 h^j - 16/12 h^{j-1}
     + 5/12 h^{j-2} (eq. h_mpea) in the midpoint update (eq. mpe_update).
     """
 

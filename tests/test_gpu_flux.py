@@ -41,7 +41,8 @@ CASES = {
                                           eps=1 / 250, box_n=32, micro_steps=30, precision=0)),
     "3d": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=16, mu_over_eps=0.9, micro_steps=20, precision=0)),
     "2d_order2": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30, stencil_order=2)),
-    # uneven boxes (N = 32..96 by eq. G15's eps field on an 8 x 8 grid): packs and clusters
+    # uneven boxes (N = 32..96 by the uneven workload's field 1/eps = 250 + 150 sin 2 pi x1 cos 2 pi x2,
+    # on an 8 x 8 grid): packs and clusters
     "2d_uneven": ("c3_2d_uneven", dict(n_macro=(8, 8, 1), micro_steps=12, precision=0)),
     # edge sizes: the smallest order-4 box (N = 2r + 2, three weighted faces per axis) and
     # the fewest micro steps with a non-zero time average (M = 2)

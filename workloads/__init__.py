@@ -9,8 +9,8 @@ Workloads follow the paper's problem statement (Section 2.1, eq. prob): a
 periodic domain [0, L]^d, a coefficient a^eps that oscillates on the scale eps,
 damping alpha and unit-length initial data (assumption A3). The named
 configurations below carry the shapes, sizes and value distributions of the
-paper's examples (Section 2.4 EX1-EX3, Section 5) at the sizes of the
-benchmark table in the design doc.
+paper's examples (Section 2.4 EX1-EX3, Section 5) at the benchmark's
+sizes.
 """
 from __future__ import annotations
 
