@@ -22,7 +22,8 @@ methods for the Landau-Lifshitz equation", step by step and in FP64:
 * HeunP time stepping (Section 3.1) with the micro time step bounded by the
   stability condition eq. Cstab (Section 3.2);
 * the field-model macro step (Section 2.2, eq. macro_disc) by MPEA
-  (Section 3.1, eqs. h_term, h_mpea, mpe_update) with an RK4P start-up.
+  (Section 3.1, eqs. h_term, h_mpea, mpe_update) or MPE (eq. h_mpe) with an
+  RK4P start-up.
 
 Where the paper is silent or garbled, the reading taken is stated where it is
 used and marked "a reading".
@@ -629,22 +630,44 @@ def midpoint_update(M: np.ndarray, h: np.ndarray, dt: float) -> np.ndarray:
     return out
 
 
+MPEA, MPE = 0, 1   # macro steppers (Section 3.1)
+
+
+def extrapolate_h(hj: np.ndarray, hist: Sequence[np.ndarray], scheme: int = MPEA) -> np.ndarray:
+    """The explicit stand-in h^{j+1/2} for h at the midpoint of step j (Section 3.1).
+
+    MPE (eq. h_mpe): 3/2 h^j - 1/2 h^{j-1}. MPEA (eq. h_mpea): 23/12 h^j -
+    16/12 h^{j-1} + 5/12 h^{j-2}. ``hist`` = [h^{j-1}, h^{j-2}] (h^{j-2} unused by MPE).
+    The coefficients are those of Adams-Bashforth 2 and 3, the methods the paper
+    links MPE and MPEA to (Section 3.2, eq. mpe_update_ab).
+    """
+    if scheme == MPE:
+        return 1.5 * hj - 0.5 * hist[0]
+    return 23.0 / 12.0 * hj - 16.0 / 12.0 * hist[0] + 5.0 / 12.0 * hist[1]
+
+
 class MacroStepper:
-    """Field-model HMM macro stepper (eq. macro_disc), MPEA with RK4P start-up.
+    """Field-model HMM macro stepper (eq. macro_disc): MPEA or MPE with RK4P start-up.
 
     ``havg(M)`` returns H_avg(x_i; M) for all macro points (default: the
-    oracle's micro_batch). Steps j = 0, 1 use RK4P (Section 3.1; the third stage
+    oracle's micro_batch). The first steps use RK4P (Section 3.1; the third stage
     read as f(M + dt/2 k2) where the printed stage repeats k_2) whose stage states
     are normalised before their micro solves (a reading: assumption A3 for the
-    micro initial data); from j = 2 on MPEA: h^{j+1/2} = 23/12 h^j - 16/12 h^{j-1}
-    + 5/12 h^{j-2} (eq. h_mpea) in the midpoint update (eq. mpe_update).
+    micro initial data): j = 0, 1 for MPEA, which needs h^{j-1} and h^{j-2}, and
+    j = 0 for MPE, which needs h^{j-1} only (Section 3.1: the multi-step methods
+    need m^1, and m^2 for MPEA). Then h^j = H_avg + alpha M x H_avg (eq. h_term),
+    h^{j+1/2} by ``extrapolate_h`` and the midpoint update (eq. mpe_update).
+    ``scheme``: MPEA (0) or MPE (1); default the config's ``macro_stepper``.
     """
 
-    def __init__(self, cfg, M0: np.ndarray, havg=None, dt: Optional[float] = None):
+    def __init__(self, cfg, M0: np.ndarray, havg=None, dt: Optional[float] = None,
+                 scheme: Optional[int] = None):
         self.cfg = cfg
         self.M = np.array(M0, dtype=np.float64, copy=True)
         self.havg = havg if havg is not None else (lambda M: micro_batch(cfg, M))
         self.dt = macro_dt(cfg) if dt is None else dt
+        self.scheme = int(getattr(cfg, "macro_stepper", MPEA) if scheme is None else scheme)
+        self.n_startup = 1 if self.scheme == MPE else 2
         self.j = 0
         self.hist: List[np.ndarray] = []   # [h^{j-1}, h^{j-2}]
 
@@ -653,7 +676,7 @@ class MacroStepper:
 
     def step(self):
         a, dt, M = self.cfg.alpha, self.dt, self.M
-        if self.j < 2:
+        if self.j < self.n_startup:
             H1 = self.havg(M)
             hj = h_term(M, H1, a)
             k1 = self._f(M, H1)
@@ -666,8 +689,7 @@ class MacroStepper:
             self.M = _normalise(M + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4))
         else:
             hj = h_term(M, self.havg(M), a)
-            hh = 23.0 / 12.0 * hj - 16.0 / 12.0 * self.hist[0] + 5.0 / 12.0 * self.hist[1]
-            self.M = midpoint_update(M, hh, dt)
+            self.M = midpoint_update(M, extrapolate_h(hj, self.hist, self.scheme), dt)
         self.hist = [hj] + self.hist[:1]
         self.j += 1
         return self.M
