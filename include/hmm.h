@@ -59,6 +59,16 @@ typedef enum {
   HMM_RK4P = 1
 } hmm_micro_stepper;
 
+/* Macro time stepper (Section 3.1): MPEA, the extrapolation of eq. h_mpea in the
+ * midpoint update of eq. mpe_update, with two RK4P start-up steps; or MPE, the
+ * extrapolation of eq. h_mpe (3/2 h^j - 1/2 h^{j-1}) with one RK4P start-up step.
+ * Both are second order; the paper prefers MPEA (better stability for low damping,
+ * Section 3.2, and third order observed on its 1D example). */
+typedef enum {
+  HMM_MPEA = 0,
+  HMM_MPE = 1
+} hmm_macro_stepper;
+
 /* The HMM macro model (Section 2.2). The field model averages H = div(a^eps grad m)
  * over each micro problem (eq. upscaling) and steps eq. macro_disc with it. The
  * flux model (eq. macro_flux) averages the flux a^eps grad m instead: column k of
@@ -122,7 +132,8 @@ typedef struct {
   int micro_stepper;            /* hmm_micro_stepper; RK4P runs on the generic
                                    kernels (kernel_variant 0 selects them)         */
   int model;                    /* hmm_model                                       */
-  int reserved[2];              /* must be zero                                    */
+  int macro_stepper;            /* hmm_macro_stepper (0: MPEA, 1: MPE)             */
+  int reserved;                 /* must be zero                                    */
 } hmm_params;
 
 /* Set-up (host only, plus device allocations on the current device).
@@ -149,6 +160,20 @@ hmm_status hmm_init(const hmm_params* params, void* cuda_stream, void** handle_o
  * With the flux model, Havg_dev receives div F_avg (see hmm_model). */
 hmm_status hmm_micro_batch(void* handle, const double* M_dev, double* Havg_dev);
 
+/* The micro batch on a subset of the macro points (field model): H_avg,i of
+ * eq. upscaling for the n_points macro points listed in points_host (a host
+ * array of distinct indices in [0, P)), written to Havg_dev at those points; the
+ * other entries of Havg_dev are left as they were. The boxes run on the generic
+ * persistent kernel of the handle's precision form (the shared-memory-resident
+ * kernels' work plans cover whole batches), so the FP64 method and the FP32 form
+ * can be sampled on batches too large to solve whole (accuracy checks at full
+ * size, timing the FP64 method on a sample). hmm_stats' last_batch_ms is this
+ * call's device time. Allocates (and keeps until hmm_destroy) a box table and an
+ * arena sized for the largest subset so far. HMM_ERR_INVALID_ARG for a flux-model
+ * handle, an index out of range or listed twice. Synchronises the stream. */
+hmm_status hmm_micro_batch_points(void* handle, const double* M_dev, double* Havg_dev, const int* points_host,
+                                  int n_points);
+
 /* Flux model only: the averaged fluxes themselves. F_dev: d x 3 x P FP64 device
  * buffer; entry [(k*3 + c)*P + p] is component c of column k of F_avg at
  * x_p + (DX_k/2) e_k, averaging a^eps D_s m along axis k over that axis's faces
@@ -161,18 +186,19 @@ hmm_status hmm_flux_batch(void* handle, const double* M_dev, double* F_dev);
 hmm_status hmm_micro_batch_host(void* handle, const double* M_host, double* Havg_host);
 
 /* n_steps macro steps of the field model (eq. macro_disc), in place on M_dev
- * (SoA 3 x P FP64). Steps j = 0 and 1 use RK4P (Section 3.1) with one micro
- * batch per stage at the normalised stage state; later steps use MPEA
- * (eqs. h_term, h_mpea, mpe_update), one micro batch per step. MPEA steps are
- * replayed from a CUDA graph captured on first use for this M_dev. */
+ * (SoA 3 x P FP64). The start-up steps (j = 0 and 1 for MPEA, j = 0 for MPE) use
+ * RK4P (Section 3.1) with one micro batch per stage at the normalised stage
+ * state; later steps use MPEA (eqs. h_term, h_mpea, mpe_update) or MPE (eq. h_mpe
+ * in place of eq. h_mpea), one micro batch per step, replayed from a CUDA graph
+ * captured on first use for this M_dev. */
 hmm_status hmm_macro_step(void* handle, double* M_dev, int n_steps);
 
 /* As hmm_macro_step with M in host memory (copied in and out once per call). */
 hmm_status hmm_macro_step_host(void* handle, double* M_host, int n_steps);
 
-/* Restart state of the macro stepper: the MPEA history hist (2 x 3 x P FP64
- * device buffer: h^{j-1} then h^{j-2}, eq. h_term) and the step count j. The
- * macro field itself is the caller's M. get copies out, set copies in. */
+/* Restart state of the macro stepper: the history hist (2 x 3 x P FP64 device
+ * buffer: h^{j-1} then h^{j-2}, eq. h_term; MPE reads only h^{j-1}) and the step
+ * count j. The macro field itself is the caller's M. get copies out, set copies in. */
 hmm_status hmm_get_state(void* handle, double* hist_dev, long long* j);
 hmm_status hmm_set_state(void* handle, const double* hist_dev, long long j);
 
@@ -207,9 +233,8 @@ hmm_status hmm_macro_dt(void* handle, double* dt_macro);
  *
  * It is for callers that must not allocate device memory: code that runs inside
  * a memory allocator's own callbacks (where cudaMalloc would re-enter the
- * allocator), applications whose device memory is fully reserved up front by
- * another framework's memory pool (so cudaMalloc fails), and latency-critical
- * paths that cannot afford cudaMalloc/cudaFree, which may synchronise the device.
+ * allocator), and applications whose device memory is fully reserved up front by
+ * another framework's memory pool (so cudaMalloc fails).
  * It takes the problem directly (no handle), runs the same batched FP32 micro
  * solve as hmm_micro_batch with kernel_variant 1, and calls no cudaMalloc,
  * cudaFree or other allocating routine: every buffer it needs (box table,
@@ -227,11 +252,15 @@ hmm_status hmm_macro_dt(void* handle, double* dt_macro);
  * synchronises it before returning. Errors are reported through
  * hmm_last_error(NULL).
  *
+ * The call copies host data to the device, reads the error word back and
+ * synchronises its stream; on a stream that is being captured it returns
+ * HMM_ERR_INVALID_ARG before enqueuing anything, and the capture stays valid.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) once for that device; make that first call before
  * any stream capture begins. All calls share the one array and each call
  * overwrites it: calls that overlap on the GPU (other threads, other streams)
- * race and must be serialised by the caller. */
+ * race and must be serialised by the caller. hmm_last_error(NULL) is cleared
+ * by a successful call. */
 hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const double* M_dev, double* Havg_dev,
                                    void* cuda_stream);
 

@@ -23,7 +23,7 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
             "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
             "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
-            "hmm_flux_batch", "hmm_plan_report", "hmm_last_error", "hmm_destroy")
+            "hmm_flux_batch", "hmm_micro_batch_points", "hmm_plan_report", "hmm_last_error", "hmm_destroy")
 # The symbols include/hmm_dns.h declares.
 EXPORTED_DNS = ("hmm_dns_init", "hmm_dns_set_face_table", "hmm_dns_step", "hmm_dns_step_host",
                 "hmm_dns_reset", "hmm_dns_info", "hmm_dns_plan", "hmm_dns_last_error", "hmm_dns_destroy")
@@ -42,7 +42,7 @@ class HmmParams(ctypes.Structure):
                 ("pts_per_eps", c_double), ("mu_over_eps", c_double), ("micro_steps", c_int),
                 ("dt_safety", c_double), ("px", c_int), ("qx", c_int), ("pt", c_int), ("qt", c_int),
                 ("interp_order", c_int), ("stencil_order", c_int), ("precision", c_int),
-                ("kernel_variant", c_int), ("micro_stepper", c_int), ("model", c_int), ("reserved", c_int * 2)]
+                ("kernel_variant", c_int), ("micro_stepper", c_int), ("model", c_int), ("macro_stepper", c_int), ("reserved", c_int)]
 
 
 class HmmDnsParams(ctypes.Structure):
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_micro_batch.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.hmm_micro_batch_host.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.hmm_flux_batch.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.hmm_micro_batch_points.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int]
     lib.hmm_macro_step.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_macro_step_host.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_get_state.argtypes = [c_void_p, c_void_p, POINTER(c_longlong)]
@@ -155,6 +156,7 @@ def make_params(cfg, precision=None, kernel_variant=0):
     p.kernel_variant = int(kernel_variant)
     p.micro_stepper = int(getattr(cfg, "micro_stepper", 0))
     p.model = int(getattr(cfg, "model", 0))
+    p.macro_stepper = int(getattr(cfg, "macro_stepper", 0))
     return p, keep
 
 
@@ -239,6 +241,19 @@ class HMM:
         if out is None:
             out = torch.empty_like(M)
         self._check(self.lib.hmm_micro_batch(self.h, c_void_p(M.data_ptr()), c_void_p(self._field(out).data_ptr())))
+        return out
+
+    def micro_batch_points(self, M, points, out=None):
+        """H_avg at the listed macro points only (hmm_micro_batch_points); ``out``
+        (3, P) keeps its other entries. Returns out."""
+        import numpy as np
+        import torch
+        M = self._field(M)
+        if out is None:
+            out = torch.zeros_like(M)
+        pts = np.ascontiguousarray(points, dtype=np.int32)
+        self._check(self.lib.hmm_micro_batch_points(self.h, c_void_p(M.data_ptr()), c_void_p(self._field(out).data_ptr()),
+                                                    c_void_p(pts.ctypes.data), int(pts.size)))
         return out
 
     def flux_batch(self, M, out=None):

@@ -3,11 +3,19 @@
 The translation units are compiled in parallel, then linked with
 ``nvcc -shared``. Objects go to ``_build/`` next to this file; the library is
 written next to this file so that the binding loads it from the source tree.
+
+The rebuild decision is keyed on a SHA-256 of every file under csrc/ and
+include/, the compile flags, the nvcc version and the host architecture, stored beside the library in
+libhmm_gb300.so.sha256: a library copied in with the tree (built elsewhere, or
+for another machine) is rebuilt unless its recorded hash matches this tree and
+this compiler. Each call prints one line saying whether it compiled.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -17,6 +25,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhmm_gb300.so")
+STAMP = LIB + ".sha256"
 SOURCES = ["hmm_api.cu", "macro.cu", "micro_fp64.cu", "micro_fp32.cu", "micro_fp32_2d.cu", "noalloc.cu",
            "res2d_pack.cu", "res2d_cluster_a.cu", "res2d_cluster_b.cu", "res2d_any.cu",
            "res3d.cu", "dns.cu"]
@@ -31,16 +40,29 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhmm_gb300.so")
 
 
-def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
-    return max(os.path.getmtime(f) for f in files)
+def _source_hash(nvcc: str) -> str:
+    h = hashlib.sha256()
+    for d in (CSRC, INCLUDE):
+        for f in sorted(os.listdir(d)):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    h.update(" ".join(SOURCES + ARCH + FLAGS[:-1]).encode())   # flags without the include path
+    ver = subprocess.run([nvcc, "--version"], capture_output=True, text=True).stdout
+    h.update(ver.encode())
+    h.update(platform.machine().encode())   # a library built on another host architecture never matches
+    return h.hexdigest()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if stale) and return the path of libhmm_gb300.so."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
+    """Compile (unless the recorded source hash matches) and return the path of libhmm_gb300.so."""
     nvcc = _nvcc()
+    digest = _source_hash(nvcc)
+    if not force and os.path.exists(LIB) and os.path.exists(STAMP):
+        with open(STAMP) as fh:
+            if fh.read().strip() == digest:
+                print(f"libhmm_gb300.so up to date (sources {digest[:12]})", file=sys.stderr)
+                return LIB
     os.makedirs(BUILD, exist_ok=True)
 
     def compile_one(src):
@@ -61,6 +83,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(digest + "\n")
+    print(f"libhmm_gb300.so compiled from source (sources {digest[:12]})", file=sys.stderr)
     return LIB
 
 

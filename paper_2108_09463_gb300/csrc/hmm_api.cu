@@ -299,6 +299,12 @@ struct HmmHandle {
   const double* graph_M = nullptr;
   std::string err;
   MicroArgs args{};
+  // hmm_micro_batch_points: box table and generic-kernel arena of the last subset
+  std::vector<int> box_of_point;   // index into boxes of macro point p's box (field model)
+  BoxDesc* d_sub_boxes = nullptr;
+  int sub_cap = 0;
+  char* d_sub_arena = nullptr;
+  size_t sub_arena_bytes = 0;
 };
 
 namespace {
@@ -322,7 +328,8 @@ hmm_status cuda_fail(HmmHandle* h, cudaError_t e, const char* where) {
 void free_all(HmmHandle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   void* ptrs[] = {h->d_boxes, h->d_F, h->d_W64, h->d_W32, h->d_w64, h->d_w32, h->d_om32, h->d_arena, h->d_queue, h->d_items, h->d_faces, h->d_face_off,
-                  h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost};
+                  h->d_err, h->d_H, h->d_hist, h->d_acc, h->d_stage, h->d_Mhost, h->d_Hhost,
+                  h->d_sub_boxes, h->d_sub_arena};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
@@ -474,8 +481,9 @@ hmm_status tune_resident_plan(HmmHandle* h) {
 hmm_status build(HmmHandle* h) {
   hmm_params& p = h->p;
   if (p.dim < 1 || p.dim > 3) return fail(h, HMM_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
-  for (int i = 0; i < 2; ++i)
-    if (p.reserved[i] != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.reserved != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.macro_stepper != HMM_MPEA && p.macro_stepper != HMM_MPE)
+    return fail(h, HMM_ERR_INVALID_ARG, "macro_stepper must be 0 (MPEA) or 1 (MPE)");
   if (p.model != HMM_FIELD_MODEL && p.model != HMM_FLUX_MODEL)
     return fail(h, HMM_ERR_INVALID_ARG, "model must be 0 (field) or 1 (flux)");
 
@@ -754,6 +762,19 @@ hmm_status build(HmmHandle* h) {
     const hmm_status st = tune_resident_plan(h);
     if (st != HMM_OK) return st;
   }
+  if (h->res2d && h->dim == 3) {
+    // the 3D launch groups: kernel, box size, CTAs per cluster (chosen by occupancy for
+    // the z-column kernel), CTAs launched, threads per CTA
+    std::string rep;
+    for (const Res2dGroup& g : h->plan.groups) {
+      char line[160];
+      std::snprintf(line, sizeof line, "3D %s: N=%d cluster=%d grid=%d threads=%d items=%d\n",
+                    g.N > 0 ? "z-column kernel" : "z-slab kernel", g.N > 0 ? g.N : h->boxes[h->plan.items[g.first_item].x].N,
+                    g.cs, g.grid, g.threads, g.n_items);
+      rep += line;
+    }
+    h->plan_report = rep;
+  }
   return HMM_OK;
 }
 
@@ -791,7 +812,8 @@ hmm_status check_error_word(HmmHandle* h) {
 hmm_status enqueue_mpea_step(HmmHandle* h, double* M) {
   hmm_status s = enqueue_micro(h, M, h->d_H);
   if (s != HMM_OK) return s;
-  cudaError_t e = launch_mpea_update(M, h->d_H, h->d_hist, h->p.alpha, h->dt_macro, h->P, h->stream);
+  cudaError_t e = launch_mpea_update(M, h->d_H, h->d_hist, h->p.alpha, h->dt_macro, h->p.macro_stepper, h->P,
+                                     h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "mpea kernel launch");
   return HMM_OK;
 }
@@ -911,6 +933,84 @@ hmm_status hmm_flux_batch(void* handle, const double* M_dev, double* F_dev) {
   return s;
 }
 
+hmm_status hmm_micro_batch_points(void* handle, const double* M_dev, double* Havg_dev, const int* points_host,
+                                  int n_points) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_dev || !Havg_dev || (n_points > 0 && !points_host))
+    return fail(h, HMM_ERR_INVALID_ARG, "null pointer");
+  if (h->p.model != HMM_FIELD_MODEL) return fail(h, HMM_ERR_INVALID_ARG, "hmm_micro_batch_points needs a field-model handle");
+  if (n_points < 0 || n_points > h->P) return fail(h, HMM_ERR_INVALID_ARG, "n_points must be 0..P");
+  if (h->box_of_point.empty()) {
+    h->box_of_point.assign(h->P, -1);
+    for (int b = 0; b < h->nb; ++b) h->box_of_point[h->boxes[b].p] = b;
+  }
+  std::vector<char> seen(h->P, 0);
+  std::vector<BoxDesc> sub;
+  sub.reserve(n_points);
+  int nmax = 0;
+  for (int i = 0; i < n_points; ++i) {
+    const int pt = points_host[i];
+    if (pt < 0 || pt >= h->P) return fail(h, HMM_ERR_INVALID_ARG, "macro point index out of range");
+    if (seen[pt]) return fail(h, HMM_ERR_INVALID_ARG, "macro point listed twice");
+    seen[pt] = 1;
+    sub.push_back(h->boxes[h->box_of_point[pt]]);
+    nmax = std::max(nmax, sub.back().N);
+  }
+  if (n_points == 0) return HMM_OK;
+  std::stable_sort(sub.begin(), sub.end(), [](const BoxDesc& x, const BoxDesc& y) { return x.N > y.N; });
+  // The generic persistent kernel of the handle's precision over just these boxes.
+  const int block = 256;
+  const size_t smem = micro_smem_bytes(h->dim, nmax, h->interp_k, h->p.n_terms);
+  int per_sm = 0;
+  HMM_CUDA(h, h->p.precision == HMM_FP64_PLAIN ? prepare_micro_fp64(h->dim, h->radius, block, smem, &per_sm)
+                                                : prepare_micro_fp32(h->dim, h->radius, block, smem, &per_sm));
+  if (per_sm < 1) return fail(h, HMM_ERR_INVALID_ARG, "micro kernel does not fit on an SM for this box size");
+  const size_t slot = h->p.precision == HMM_FP64_PLAIN ? micro_slot_bytes_fp64(h->dim, nmax)
+                                                        : micro_slot_bytes_fp32(h->dim, nmax);
+  const int grid = std::min(n_points, per_sm * h->num_sms);
+  HMM_TRY(begin_call(h));
+  if (n_points > h->sub_cap) {
+    HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->d_sub_boxes) cudaFree(h->d_sub_boxes);
+    h->d_sub_boxes = nullptr;
+    h->sub_cap = 0;
+    HMM_CUDA(h, cudaMalloc(&h->d_sub_boxes, sizeof(BoxDesc) * n_points));
+    h->sub_cap = n_points;
+  }
+  if (slot * grid > h->sub_arena_bytes) {
+    HMM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->d_sub_arena) cudaFree(h->d_sub_arena);
+    h->d_sub_arena = nullptr;
+    h->sub_arena_bytes = 0;
+    HMM_CUDA(h, cudaMalloc(&h->d_sub_arena, slot * grid));
+    h->sub_arena_bytes = slot * grid;
+  }
+  HMM_CUDA(h, cudaMemcpyAsync(h->d_sub_boxes, sub.data(), sizeof(BoxDesc) * n_points, cudaMemcpyHostToDevice,
+                              h->stream));
+  HMM_CUDA(h, cudaStreamSynchronize(h->stream));   // the host vector goes out of scope
+  HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int) * kQueues, h->stream));
+  MicroArgs a = h->args;
+  a.boxes = h->d_sub_boxes;
+  a.n_boxes = n_points;
+  a.arena = h->d_sub_arena;
+  a.slot_bytes = slot;
+  a.nmax = nmax;
+  a.M = M_dev;
+  a.Havg = Havg_dev;
+  HMM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  cudaError_t e = h->p.precision == HMM_FP64_PLAIN ? launch_micro_fp64(a, h->dim, h->radius, grid, block, smem, h->stream)
+                                                    : launch_micro_fp32(a, h->dim, h->radius, grid, block, smem, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "micro kernel launch");
+  HMM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  HMM_TRY(end_call(h));
+  hmm_status s = check_error_word(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->last_ms = ms;
+  return s;
+}
+
 hmm_status hmm_micro_batch_host(void* handle, const double* M_host, double* Havg_host) {
   HmmHandle* h = as_handle(handle);
   if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
@@ -933,7 +1033,7 @@ hmm_status hmm_macro_step(void* handle, double* M_dev, int n_steps) {
   HMM_TRY(begin_call(h));
   for (int s = 0; s < n_steps; ++s) {
     hmm_status st;
-    if (h->j < 2) {
+    if (h->j < (h->p.macro_stepper == HMM_MPE ? 1 : 2)) {
       st = enqueue_rk4_step(h, M_dev);
     } else {
       st = ensure_graph(h, M_dev);
@@ -1078,6 +1178,28 @@ hmm_status hmm_set_face_table(void* handle, const double* table_host, long long 
   }
   h->args.faces = h->d_faces;
   h->args.face_off = h->d_face_off;
+  if (h->res2d && h->dim == 3 && res3d_plan_uses_col3(h->plan)) {
+    // the z-column kernel evaluates separable coefficient terms in its time loop:
+    // tabulated coefficients run on the z-slab kernel, which reads the set-up's faces
+    Res2dPlan pl;
+    std::string why;
+    if (!res2d_make_plan(3, h->boxes.data(), h->nb, h->radius, h->interp_k, p.n_terms, h->plan.smem, &pl, &why,
+                         nullptr, false))
+      return fail(h, HMM_ERR_INVALID_ARG, why);
+    HMM_CUDA(h, res2d_prepare(h->radius, &pl, h->num_sms));
+    const int grid = res2d_max_grid(pl);
+    if (grid > h->grid) {
+      char* ar = nullptr;
+      HMM_CUDA(h, cudaMalloc(&ar, h->slot_bytes * (size_t)grid));
+      cudaFree(h->d_arena);
+      h->d_arena = ar;
+      h->args.arena = ar;
+      h->grid = grid;
+    }
+    if (pl.items.size() != h->plan.items.size()) return fail(h, HMM_ERR_INVALID_ARG, "3D work items changed size");
+    HMM_CUDA(h, cudaMemcpy(h->d_items, pl.items.data(), sizeof(int2) * pl.items.size(), cudaMemcpyHostToDevice));
+    h->plan = pl;
+  }
   if (h->graph) {   // captured with the old arguments
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;

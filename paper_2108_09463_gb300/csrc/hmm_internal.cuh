@@ -98,6 +98,9 @@ struct Res2dGroup {
   int first_item;
   int n_items;
   int grid;         // CTAs launched (a multiple of cs), set by res2d_prepare
+  int threads;      // threads per CTA
+  int aux;          // z-column 3D kernel: row stride of its planes; 0 otherwise
+  int N;            // z-column 3D kernel: the group's box size; 0 otherwise
 };
 struct Res2dPlan {
   std::vector<int2> items;
@@ -108,9 +111,13 @@ struct Res2dPlan {
 // False (with the reason) when some box fits no cluster of the portable size.
 // pick: per box size N, the (instance, cluster size) to use instead of the
 // heuristic's choice (the autotuner's result), or NULL.
+// allow_col3: 3D boxes may run on the z-column kernel, which evaluates separable
+// coefficient terms in its time loop (false once a face table is set).
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
                      Res2dPlan* plan, std::string* why,
-                     const std::map<int, std::pair<int, int>>* pick = nullptr);
+                     const std::map<int, std::pair<int, int>>* pick = nullptr, bool allow_col3 = true);
+// True when a 3D plan runs any group on the z-column kernel.
+bool res3d_plan_uses_col3(const Res2dPlan& plan);
 // The (instance, cluster size) pairs that hold a 2D box of N nodes, the
 // heuristic's choice first; the canvas size of an instance (0: box stride).
 std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes);
@@ -125,8 +132,9 @@ cudaError_t res2d_launch(const MicroArgs& a, int radius, const Res2dPlan& plan, 
 // Macro-side kernels (FP64, pointwise over P points).
 cudaError_t launch_h_term(const double* M, const double* H, double alpha, double* h, int P,
                           cudaStream_t st);
+// scheme: hmm_macro_stepper (0 MPEA, 1 MPE), which fixes the extrapolation of h^{j+1/2}.
 cudaError_t launch_mpea_update(double* M, const double* H, double* hist, double alpha,
-                               double dt, int P, cudaStream_t st);
+                               double dt, int scheme, int P, cudaStream_t st);
 // RK4P: k = f(Ms, H); acc += wk*k (acc = 0 when first); Mnext = normalise(M + c*k).
 cudaError_t launch_rk4_stage(const double* M, const double* Ms, const double* H, double alpha,
                              double dt, int stage, double* acc, double* Mnext, double* hist0,

@@ -1,7 +1,8 @@
 // Macro-side kernels of the field model (Section 2.2, eq. macro_disc), FP64,
 // one thread per macro point:
 //  - MPEA: h^j = H + alpha M x H (eq. h_term), h^{j+1/2} = 23/12 h^j - 16/12
-//    h^{j-1} + 5/12 h^{j-2} (eq. h_mpea), and the midpoint update
+//    h^{j-1} + 5/12 h^{j-2} (eq. h_mpea) (MPE: 3/2 h^j - 1/2 h^{j-1}, eq. h_mpe),
+//    and the midpoint update
 //    (M' - M)/dt = -(M + M')/2 x h^{j+1/2} (eq. mpe_update), solved in closed
 //    form: with w = dt/2 h, (I - [w]x) M' = (I + [w]x) M, whose solution is
 //    M' = M + 2/(1 + |w|^2) (w x M + w x (w x M)).
@@ -39,7 +40,8 @@ __global__ void h_term_kernel(const double* M, const double* H, double alpha, do
   store3(h, P, p, c);
 }
 
-__global__ void mpea_kernel(double* M, const double* H, double* hist, double alpha, double dt, int P) {
+__global__ void mpea_kernel(double* M, const double* H, double* hist, double alpha, double dt, double c0, double c1,
+                            double c2, int P) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double m[3], Hv[3], c[3], h1[3], h2[3], hj[3], w[3];
@@ -50,7 +52,7 @@ __global__ void mpea_kernel(double* M, const double* H, double* hist, double alp
   cross3(m, Hv, c);
   for (int i = 0; i < 3; ++i) hj[i] = Hv[i] + alpha * c[i];
   for (int i = 0; i < 3; ++i)
-    w[i] = 0.5 * dt * ((23.0 / 12.0) * hj[i] - (16.0 / 12.0) * h1[i] + (5.0 / 12.0) * h2[i]);
+    w[i] = 0.5 * dt * (c0 * hj[i] + c1 * h1[i] + c2 * h2[i]);
   double wm[3], wwm[3];
   cross3(w, m, wm);
   cross3(w, wm, wwm);
@@ -162,8 +164,12 @@ cudaError_t launch_h_term(const double* M, const double* H, double alpha, double
 }
 
 cudaError_t launch_mpea_update(double* M, const double* H, double* hist, double alpha, double dt,
-                               int P, cudaStream_t st) {
-  mpea_kernel<<<nblk(P), 256, 0, st>>>(M, H, hist, alpha, dt, P);
+                               int scheme, int P, cudaStream_t st) {
+  // extrapolation coefficients of h^j, h^{j-1}, h^{j-2}: MPE (scheme 1), else MPEA
+  const double c0 = scheme == 1 ? 1.5 : 23.0 / 12.0;
+  const double c1 = scheme == 1 ? -0.5 : -16.0 / 12.0;
+  const double c2 = scheme == 1 ? 0.0 : 5.0 / 12.0;
+  mpea_kernel<<<nblk(P), 256, 0, st>>>(M, H, hist, alpha, dt, c0, c1, c2, P);
   return cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 #include <string>
 #include <vector>
 
-#include "micro_fp32_3d.cuh"
+#include "micro_fp32_3d_col.cuh"
 
 #include <map>
 #include <utility>
@@ -37,13 +37,32 @@ const std::vector<ResVariant>& variants(int dim) {
   return dim == 3 ? all3 : all2;
 }
 
-// 3D: the first canvas that holds the box (its cluster size is fixed), if its slabs fit.
-bool choose3(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out) {
+// 3D: the z-column kernel when it may run and holds the box (slabs of 3 to kCol3S
+// planes, at most kCol3MaxTerms separable terms), else the first z-slab canvas that
+// holds the box (its cluster size is fixed), if its slabs fit.
+bool choose3(int N, int R, int interp_k, int n_terms, size_t budget, bool allow_col3, int* vi, int* cs_out) {
   const auto& V = variants(3);
   const int Ni = N - 2 * R;
   for (int i = 0; i < (int)V.size(); ++i) {
     const ResVariant& v = V[i];
-    if (v.R != R || v.NC < N || v.cs > Ni) continue;
+    if (v.TZ >= 0 || !allow_col3 || v.R != R || N > v.NC || n_terms > kCol3MaxTerms) continue;
+    const int cs = (Ni + kCol3S - 1) / kCol3S;   // the fewest CTAs; res2d_prepare may take more
+    if (cs > 16) continue;
+    int LD = 0, hw = 0;
+    col3_layout(N, &LD, &hw);
+    const int NT = (16 * hw + 31) / 32 * 32;
+    // small boxes leave a column CTA with few warps: those run on the z-slab kernel
+    if (NT > kCol3MaxThreads || NT < 256) continue;
+    const Col3Offsets o = col3_offsets(N, LD, NT);
+    if ((size_t)o.total + kResHeaderFloats > budget) continue;
+    if (setup_smem_doubles(3, N, interp_k, n_terms) * 2 > (size_t)3 * kCol3S * N * LD) continue;
+    *vi = i;
+    *cs_out = cs;
+    return true;
+  }
+  for (int i = 0; i < (int)V.size(); ++i) {
+    const ResVariant& v = V[i];
+    if (v.TZ < 0 || v.R != R || v.NC < N || v.cs > Ni) continue;
     const int Sa = (Ni + v.cs - 1) / v.cs;
     if (Sa > v.SAC) continue;
     const Res3Dims d = res3_dims(v.NC, R, v.SAC);
@@ -142,8 +161,16 @@ std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, in
 
 int res2d_variant_canvas(int vi) { return variants(2)[vi].NC; }
 
+bool res3d_plan_uses_col3(const Res2dPlan& plan) {
+  if (plan.dim != 3) return false;
+  for (const Res2dGroup& g : plan.groups)
+    if (variants(3)[g.variant].TZ < 0) return true;
+  return false;
+}
+
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
-                     Res2dPlan* plan, std::string* why, const std::map<int, std::pair<int, int>>* pick) {
+                     Res2dPlan* plan, std::string* why, const std::map<int, std::pair<int, int>>* pick,
+                     bool allow_col3) {
   const size_t budget = smem_bytes / sizeof(float);
   const auto& V = variants(2);
   plan->items.clear();
@@ -166,12 +193,19 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
   while (i < n) {
     int vi = -1, cs = 0;
     if (dim == 3) {
-      if (!choose3(boxes[i].N, R, interp_k, n_terms, budget, &vi, &cs)) {
-        *why = "no 3D resident instance holds a box of N = " + std::to_string(boxes[i].N) + " with this stencil";
+      const int N = boxes[i].N;
+      if (!choose3(N, R, interp_k, n_terms, budget, allow_col3, &vi, &cs)) {
+        *why = "no 3D resident instance holds a box of N = " + std::to_string(N) + " with this stencil";
         return false;
       }
-      if (plan->groups.empty() || plan->groups.back().variant != vi)
-        plan->groups.push_back(Res2dGroup{cs, vi, (int)plan->items.size(), 0, 0});
+      const bool col3 = variants(3)[vi].TZ < 0;
+      int LD = 0, hw = 0;
+      if (col3) col3_layout(N, &LD, &hw);
+      const int threads = col3 ? (16 * hw + 31) / 32 * 32 : kResThreads;
+      // one group per instance and cluster size (the z-column kernel: per box size)
+      if (plan->groups.empty() || plan->groups.back().variant != vi || plan->groups.back().cs != cs ||
+          (col3 && plan->groups.back().N != N))
+        plan->groups.push_back(Res2dGroup{cs, vi, (int)plan->items.size(), 0, 0, threads, LD, col3 ? N : 0});
       plan->items.push_back(make_int2(i, 1));
       plan->groups.back().n_items++;
       ++i;
@@ -202,7 +236,7 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
       }
     }
     if (plan->groups.empty() || plan->groups.back().variant != vi || plan->groups.back().cs != cs)
-      plan->groups.push_back(Res2dGroup{cs, vi, (int)plan->items.size(), 0, 0});
+      plan->groups.push_back(Res2dGroup{cs, vi, (int)plan->items.size(), 0, 0, kResThreads, 0, 0});
     plan->items.push_back(make_int2(i, k));
     plan->groups.back().n_items++;
     i += k;
@@ -218,7 +252,7 @@ static cudaLaunchConfig_t launch_config(const Res2dGroup& g, int grid, size_t sm
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kResThreads);
+  cfg.blockDim = dim3(g.threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = at;
@@ -233,13 +267,51 @@ cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms) {
     const void* fn = reinterpret_cast<const void*>(V[g.variant].fn);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
     if (e != cudaSuccess) return e;
+    if (V[g.variant].TZ < 0) {
+      // z-column kernel: the cluster size that finishes boxes fastest, the clusters the
+      // GPU holds at once (whole clusters per GPC) over the planes of the largest slab
+      const int Ni = g.N - 2 * V[g.variant].R;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      double best = -1.0;
+      int best_cs = 0, best_cl = 0;
+      for (int cs = 1; cs <= 16 && cs <= Ni; ++cs) {
+        const int smax = (Ni + cs - 1) / cs;
+        if (smax > kCol3S) continue;
+        Res2dGroup t = g;
+        t.cs = cs;
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = launch_config(t, cs * num_sms, plan->smem, 0, at);
+        int clusters = 0;
+        if (cs == 1) {
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&clusters, fn, g.threads, plan->smem);
+          clusters *= num_sms;
+        } else {
+          e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+        }
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        const double score = (double)std::min(clusters, g.n_items) / smax;
+        if (clusters > 0 && score > best) {
+          best = score;
+          best_cs = cs;
+          best_cl = clusters;
+        }
+      }
+      if (best_cs == 0) return cudaErrorInvalidConfiguration;
+      g.cs = best_cs;
+      g.grid = std::min(g.n_items, best_cl) * best_cs;
+      continue;
+    }
     if (g.cs > 8) {   // clusters beyond the portable size of 8
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
     if (g.cs == 1) {
       int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kResThreads, plan->smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, plan->smem);
       if (e != cudaSuccess) return e;
       if (per_sm < 1) return cudaErrorInvalidConfiguration;
       g.grid = std::min(g.n_items, per_sm * num_sms);
@@ -268,7 +340,7 @@ cudaError_t res2d_launch(const MicroArgs& a, int radius, const Res2dPlan& plan, 
   const auto& V = variants(plan.dim);
   for (size_t gi = 0; gi < plan.groups.size(); ++gi) {
     const Res2dGroup& g = plan.groups[gi];
-    const ResLaunch L{d_items + g.first_item, g.n_items, d_queues + gi, g.cs};
+    const ResLaunch L{d_items + g.first_item, g.n_items, d_queues + gi, g.cs, g.aux};
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = launch_config(g, g.grid, plan.smem, st, at);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, V[g.variant].fn, a, L);

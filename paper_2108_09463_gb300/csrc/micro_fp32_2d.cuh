@@ -176,6 +176,7 @@ struct ResLaunch {
   int n_items;
   int* queue;
   int cs;
+  int aux;   // z-column 3D kernel: the row stride of its planes (0 otherwise)
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -741,7 +742,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
 struct ResVariant {
   int R, NC, SAC, cs;
   void (*fn)(MicroArgs, ResLaunch);
-  int TZ;   // 3D: planes per thread tile (0 for 2D)
+  int TZ;   // 3D: planes per thread tile (0 for 2D; -1: the z-column kernel, cs chosen per box)
 };
 
 int res2d_variants_pack(const ResVariant** v);

@@ -1,8 +1,8 @@
 // Allocation-free variant of the batched FP32 micro solve.
 //
-// Some callers cannot allocate device memory: code running inside a stream
-// capture it does not own, inside a custom allocator's callback, or in a process
-// whose device memory is fully reserved by another framework. hmm_init allocates
+// Some callers cannot allocate device memory: code running inside a custom
+// allocator's callback (where cudaMalloc would re-enter the allocator), or in a
+// process whose device memory is fully reserved by another framework. hmm_init allocates
 // (box tables, weight tables, per-CTA arenas), so those callers get
 // hmm_micro_batch_noalloc instead: it runs the same FP32 micro kernel with every
 // buffer it needs carved out of one file-scope device array of fixed size,
@@ -102,6 +102,16 @@ using namespace hmm;
 extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const double* M_dev,
                                              double* Havg_dev, void* cuda_stream) {
   if (!params || !M_dev || !Havg_dev) return noalloc_fail(HMM_ERR_INVALID_ARG, "null argument");
+  {
+    // The call copies host data in, reads the error word back and synchronises its
+    // stream, so a stream that is being captured is refused before anything is
+    // enqueued (the capture stays valid).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NA_CUDA(cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+      return noalloc_fail(HMM_ERR_INVALID_ARG,
+                          "the allocation-free entry point cannot run on a stream that is being captured");
+  }
   hmm_params p = *params;
   char msg[256];
   if (p.dim < 1 || p.dim > 3) return noalloc_fail(HMM_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
@@ -109,8 +119,9 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point runs the FP32 form only");
   if (p.eps_field || p.box_n_field)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point needs uniform eps and N");
-  for (int i = 0; i < 2; ++i)
-    if (p.reserved[i] != 0) return noalloc_fail(HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.reserved != 0) return noalloc_fail(HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.macro_stepper != HMM_MPEA && p.macro_stepper != HMM_MPE)
+    return noalloc_fail(HMM_ERR_INVALID_ARG, "macro_stepper must be 0 (MPEA) or 1 (MPE)");
   if (p.model != HMM_FIELD_MODEL) return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free batch runs the field model");
   if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
@@ -292,5 +303,6 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
   NA_CUDA(cudaStreamSynchronize(stream));
   if (err & kErrCoefNonPositive) return noalloc_fail(HMM_ERR_INVALID_ARG, "coefficient a^eps <= 0 at a micro face (A1)");
   if (err) return noalloc_fail(HMM_ERR_NONFINITE, "non-finite value in the micro solve");
+  set_null_handle_error("");   // hmm_last_error(NULL) describes failures only
   return HMM_OK;
 }

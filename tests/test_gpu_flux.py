@@ -40,6 +40,7 @@ CASES = {
     "2d_slow_fast": ("c3_2d_uneven", dict(n_macro=(8, 8, 1), eps_field=None, box_n_field=None,
                                           eps=1 / 250, box_n=32, micro_steps=30, precision=0)),
     "3d": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=16, mu_over_eps=0.9, micro_steps=20, precision=0)),
+    "3d_n32": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=32, micro_steps=12, precision=0)),
     "2d_order2": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30, stencil_order=2)),
     # uneven boxes (N = 32..96 by the uneven workload's field 1/eps = 250 + 150 sin 2 pi x1 cos 2 pi x2,
     # on an 8 x 8 grid): packs and clusters

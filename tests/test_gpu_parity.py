@@ -163,6 +163,10 @@ def test_rk4p_rejected_by_resident_kernels(torch_cuda):
 # (hmm_set_face_table): the locally periodic 2D example of Section 5 and a 1D one.
 TABLE = {
     "loc2d": ("ex_loc2d", dict(n_macro=(6, 5, 1), box_n=29, mu_over_eps=0.0, micro_steps=40)),
+    # a 3D box the z-column kernel would take: the table moves it to the z-slab kernel
+    "3d_n32": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=32, micro_steps=12,
+                             coef_fn=lambda X, eps: 1.0 + 0.5 * np.sin(2 * np.pi * X[0] / eps)
+                             * np.sin(2 * np.pi * X[1] / eps) * np.cos(2 * np.pi * X[2] / eps + 0.3))),
     "loc1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=60,
                             coef_fn=lambda X, eps: 1.1 + 0.25 * np.sin(2 * np.pi * X[0] + 1.1)
                             + 0.5 * np.sin(2 * np.pi * X[0] / eps))),
@@ -263,9 +267,16 @@ def test_resident_2d_kernel_clusters(torch_cuda, case):
 
 
 # 3D boxes: each split by z-planes over a cluster (planes beyond a CTA's slab read from
-# the neighbouring CTAs' shared memory), or held by one CTA when small.
+# the neighbouring CTAs' shared memory), or held by one CTA when small: the z-column
+# kernel for 27^3 to 32^3 boxes, the z-slab kernel for smaller ones and for tabulated
+# coefficients.
 RESIDENT_3D = {
+    # the z-column kernel (boxes of 27^3 to 32^3, cluster size chosen by occupancy)
     "n32_cluster7": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=32, micro_steps=20)),
+    "n31_column_odd": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=31, micro_steps=20)),
+    "n28_column": ("c4_3d", dict(n_macro=(5, 6, 5), box_n=28, mu_over_eps=1.6, micro_steps=26)),
+    # the z-slab kernel
+
     "n21_cluster3_odd": ("c4_3d", dict(n_macro=(5, 5, 6), box_n=21, mu_over_eps=0.9, micro_steps=24)),
     "n16_one_cta": ("c4_3d", dict(n_macro=(5, 6, 5), box_n=16, mu_over_eps=0.9, micro_steps=30)),
 }
@@ -363,6 +374,9 @@ def test_full_size_sampled(torch_cuda, name, precision):
 MACRO = {
     "1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=100), 5),
     "2d": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30), 4),
+    # MPE (eq. h_mpe): one RK4P start-up step, then MPE steps
+    "1d_mpe": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=100, macro_stepper=1), 5),
+    "2d_mpe": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=30, macro_stepper=1), 4),
 }
 
 
