@@ -2,11 +2,14 @@
 """Benchmark of the HMM micro-problem path on GB300.
 
 A step is one full HMM macro step (MPEA, Section 3.1) of the field model on the
-2D workload: a 128^2 periodic macro grid, one 64^2-node micro box per macro
-point (16384 micro problems), 400 HeunP micro steps each, eps = 1/200,
-a = 1 + 0.5 sin(2 pi y1) sin(2 pi y2), alpha = 0.05, alpha_micro = 1.2,
-4th-order stencil. The headline value is micro lattice updates per second of
-the batched FP32 form; the plain FP64 method is timed on the same workload.
+3D workload at its full size: a 64^3 periodic macro grid, one 32^3-node micro
+box per macro point (262,144 micro problems), 300 HeunP micro steps each,
+eps = 1/100, a = 1 + 0.5 sin(2 pi y1) sin(2 pi y2) sin(2 pi y3), alpha = 0.1,
+alpha_micro = 1.2, 4th-order stencil: 1.38e12 lattice updates per step. The
+headline value is micro lattice updates per second of the batched FP32 form;
+the plain FP64 method is timed on a sample of the same boxes. The line carries
+the same measurements for the uneven 2D workload (256^2 macro grid, boxes of
+32^2 to 96^2) and the 128^2 2D workload as sub-objects.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,31 +39,56 @@ sys.path.insert(0, ROOT)
 
 METRIC = "micro lattice updates/s + HMM macro steps/s, FP32-batched vs FP64, <=1e-6 rel err"
 UNIT = "LU/s"
-WORKLOAD = "c2_2d"
-WORKLOAD_DESC = ("2D HMM, 128^2 periodic macro grid, 16384 micro boxes of 64^2 nodes "
-                 "(8 per eps, eps=1/200), 400 HeunP micro steps, 4th-order stencil, "
-                 "a=1+0.5sin(2pi y1)sin(2pi y2), alpha=0.05, alpha_micro=1.2")
-FLOPS_PER_LU_2D = 255.0     # algorithmic FP32 flops per lattice update, 2D order 4: stencil 120,
-                            # m = m_init + v 6, right-hand side 48, stage 1 18, stage 2 63
+WORKLOAD = "c4_3d"
+# Algorithmic FP32 flops per lattice update of HeunP with the order-4 staggered stencil
+# (no compensation terms): per stage the stencil costs 9 flops per axis and component
+# (one face flux of 5, one node combination of 4) plus 2 for H = cs Hs + H(m_init) per
+# component, the right-hand side 27 (m = m_init + v, two cross products, the damping
+# fma); the stages' combination, projection and update 42; the average 6. 2D: 2 x 60 +
+# 54 + 42 + 6 = 222; 3D: 2 x 87 + 54 + 42 + 6 = 276.
+FLOPS_PER_LU = {2: 222.0, 3: 276.0}
 BYTES_PER_LU_FP32 = 24.0    # streaming-model bytes per lattice update: 3-component FP32 state read and written
 FP32_LANES_PER_SM = 128
+WORKLOADS = {
+    "c4_3d": dict(
+        desc=("3D HMM, 64^3 periodic macro grid, 262144 micro boxes of 32^3 nodes (6 per eps, eps=1/100), "
+              "300 HeunP micro steps, 4th-order stencil, a=1+0.5 sin(2pi y1)sin(2pi y2)sin(2pi y3), "
+              "alpha=0.1, alpha_micro=1.2"),
+        kernel="micro_fp32_3d_col_kernel<3> (z-column, shared-memory resident, 9-CTA clusters)",
+        traffic="micro_fp32_3d_col_c4_traffic.txt", source="micro_fp32_3d_col.cuh",
+        steps=1, e2e_steps=1, fp64_sample=4096),
+    "c3_2d_uneven": dict(
+        desc=("2D HMM, 256^2 macro grid, 65536 uneven micro boxes of 32^2 to 96^2 nodes (eps_i in "
+              "[1/400, 1/100], 8 per eps_i), 400 HeunP micro steps, a=1.1+0.25sin(2pi y1)cos(2pi y2)"
+              "+0.25sin(2pi x1)sin(2pi y2), alpha=0.01, alpha_micro=1.2"),
+        kernel="micro_fp32_2d_kernel instances (shared-memory resident; packs and clusters)",
+        traffic=None, source="micro_fp32_2d.cuh", steps=3, e2e_steps=2, fp64_sample=1024),
+    "c2_2d": dict(
+        desc=("2D HMM, 128^2 periodic macro grid, 16384 micro boxes of 64^2 nodes (8 per eps, eps=1/200), "
+              "400 HeunP micro steps, 4th-order stencil, a=1+0.5sin(2pi y1)sin(2pi y2), alpha=0.05, "
+              "alpha_micro=1.2"),
+        kernel="micro_fp32_2d_kernel<3,4,64,58> (shared-memory resident)",
+        traffic="micro_fp32_2d_c2_traffic.txt", source="micro_fp32_2d.cuh", steps=10, e2e_steps=5,
+        fp64_sample=4096),
+}
+SUB_WORKLOADS = ("c3_2d_uneven", "c2_2d")
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "micro_fp32_2d_c2_traffic.txt")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", "micro_fp32_2d.cuh")
 DNS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dns_kernel_quasi2d_traffic.txt")
 DNS_KERNEL_SOURCE = os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", "dns_kernels.cuh")
 
 
-def _traffic_from_profile(traffic_file=None, kernel_source=None):
+def _traffic_from_profile(traffic_file, kernel_source):
     """ncu DRAM bytes per full launch recorded for this kernel source, else None.
 
     The profile summary carries the SHA-256 of the kernel source it was captured
     from; once the source changes the figure no longer applies and None is returned.
     """
+    if not traffic_file:
+        return None
     try:
-        kv = dict(line.split(":", 1) for line in open(traffic_file or TRAFFIC_FILE) if ":" in line)
-        sha = hashlib.sha256(open(kernel_source or KERNEL_SOURCE, "rb").read()).hexdigest()
+        kv = dict(line.split(":", 1) for line in open(traffic_file) if ":" in line)
+        sha = hashlib.sha256(open(kernel_source, "rb").read()).hexdigest()
         if kv["kernel_source_sha256"].strip() != sha:
             return None
         return float(kv["dram_bytes_per_full_launch"])
@@ -186,11 +214,148 @@ def aggregate_ranks(ms_local: float, world: int, steps: int, units_per_step: flo
     return ms_max, world * steps * units_per_step / (ms_max / 1e3)
 
 
-def run_ours(args, rank, world, local_rank):
+def _timed(fn, k, flush):
+    """k calls of fn, each bracketed by CUDA events on the current stream, L2 flushed
+    between them (a write larger than L2); returns the total device ms."""
+    import torch
+    tot = 0.0
+    for _ in range(k):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot
+
+
+def measure_workload(name, steps, warmup, flush, world=1, dist=None, pool=None, cpu_workers=16,
+                     cpu_boxes_per_worker=1, kernel_reps=2):
+    """The batched FP32 form on one workload: `warmup` then `steps` MPEA macro steps
+    (value = lattice updates/s over the timed steps), the dominant kernel's time per
+    launch from the library's events on its stream, the roofline, end to end through
+    the host-buffer entry point, the FP64 method on a sample of the same boxes, and
+    the oracle on a bounded sample of boxes (spawned processes on the host cores)."""
     import numpy as np
     import torch
     import workloads as W
-    from paper_2108_09463_gb300 import HMM, build
+    from paper_2108_09463_gb300 import HMM
+    spec = WORKLOADS[name]
+    cfg = W.config(name)
+    M0 = W.initial_field(cfg)
+    h32 = HMM(cfg, precision=1)
+    lu_batch, _ = h32.stats()
+    plan = h32.plan_report().strip()
+    # MPEA steps from a restart state (history zero, j = 2): every step is a full micro
+    # batch and an MPEA update; the RK4P start-up (4 micro batches a step) is not timed
+    hist = torch.zeros((2, 3, cfg.n_points), dtype=torch.float64, device="cuda")
+    h32.set_state(hist, 2)
+    M = torch.from_numpy(M0).cuda()
+    for _ in range(warmup):
+        h32.macro_step(M, 1)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = _timed(lambda: h32.macro_step(M, 1), steps, flush)
+    torch.cuda.synchronize()
+    ms_max, value = aggregate_ranks(ms, world, steps, lu_batch, dist, "cuda")
+    # the dominant kernel: one micro batch, timed per launch on the library's stream
+    H = torch.empty_like(M)
+    kms = []
+    for _ in range(kernel_reps):
+        flush.zero_()
+        h32.micro_batch(M, H)
+        kms.append(h32.stats()[1])
+    k_ms = min(kms)
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    alu_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = FLOPS_PER_LU[cfg.dim] * lu_batch
+    achieved = flops / (k_ms / 1e3) / 1e12
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    if spec["traffic"]:
+        traffic = _traffic_from_profile(os.path.join(ROOT, "profiles", spec["traffic"]),
+                                        os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", spec["source"]))
+    stream_gbs = BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": traffic, "kernel": spec["kernel"], "kernel_ms": k_ms,
+                "flops_per_lu": FLOPS_PER_LU[cfg.dim],
+                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz "
+                               "(no measured FP32 peak in MEASURED_PEAKS.json)",
+                "hbm_streaming_equivalent": {"GB_per_s": stream_gbs, "frac_of_measured_hbm": stream_gbs / hbm,
+                                             "bytes_per_lu": BYTES_PER_LU_FP32}}
+    # end to end through hmm_macro_step_host: pinned host M in and out every step
+    Mh = M.cpu().pin_memory()
+    ke = spec["e2e_steps"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        h32.macro_step_host(Mh.numpy(), 1)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * ke * lu_batch / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * cfg.n_points * 8, "d2h_bytes_per_step": 3 * cfg.n_points * 8,
+           "macro_steps_per_s": ke / e2e_s, "steps": ke, "entry_point": "hmm_macro_step_host"}
+    # the plain FP64 method: the whole batch, or a spread sample of its boxes through
+    # hmm_micro_batch_points when the whole batch would take minutes
+    h64 = HMM(cfg, precision=0)
+    nsamp = spec["fp64_sample"]
+    Mfix = torch.from_numpy(M0).cuda()
+    H32 = h32.micro_batch(Mfix).cpu().numpy()
+    info = h32.box_info()
+    if nsamp:
+        pts = np.linspace(0, cfg.n_points - 1, nsamp).astype(np.int64)
+        pts = np.unique(pts)
+        h64.micro_batch_points(Mfix, pts[:64])      # warm-up (allocates the subset tables)
+        H64f = h64.micro_batch_points(Mfix, pts).cpu().numpy()
+        ms64 = h64.stats()[1]
+        lu64_batch = float(np.sum((info["N"][pts] - 6.0) ** cfg.dim) * cfg.micro_steps)
+        sel = pts
+        fp64_desc = f"hmm_micro_batch_points on {len(pts)} boxes spread over the grid"
+    else:
+        H64f = h64.micro_batch(Mfix).cpu().numpy()
+        ms64 = h64.stats()[1]
+        lu64_batch = lu_batch
+        sel = slice(None)
+        fp64_desc = "hmm_micro_batch on the whole batch"
+    lu64 = lu64_batch / (ms64 / 1e3)
+    rel = float(np.linalg.norm(H32[:, sel] - H64f[:, sel], axis=0).max() / np.linalg.norm(H64f[:, sel], axis=0).max())
+    h64.close()
+    h32.close()
+    out = {"workload": spec["desc"], "name": name, "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms_max / steps, "macro_steps_per_s": steps / (ms_max / 1e3), "lu_per_step": lu_batch,
+           "boxes": cfg.n_points, "micro_steps": cfg.micro_steps,
+           "fp64_plain": {"value": lu64, "unit": UNIT, "how": fp64_desc, "kernel_ms": ms64},
+           "speedup_fp32_vs_fp64": value / world / lu64,
+           "fp32_vs_fp64_rel_err": rel,
+           "roofline": roofline, "e2e": e2e, "plan": plan,
+           "gpu_launches_per_step": 3, "clocks": clk.summary()}
+    if pool is not None:
+        v, sinfo = oracle_sample(name, cpu_boxes_per_worker, cpu_workers, pool)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_workers, "kind": "oracle",
+                               "sample": f"{sinfo['boxes']} of the {cfg.n_points} micro boxes (whole boxes, all "
+                                         f"{cfg.micro_steps} micro steps), {cpu_workers} spawned processes, "
+                                         f"{sinfo['wall_s']:.1f} s wall"}
+    else:
+        out["cpu_baseline"] = None
+    return out
+
+
+CPU_BOXES = {"c4_3d": 2, "c3_2d_uneven": 4, "c2_2d": 16}
+
+
+def _warm_worker(_):
+    import workloads  # noqa: F401
+    from oracle import hmm_oracle  # noqa: F401
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2108_09463_gb300 import build
 
     # Spawned CPU workers for the oracle baseline start before any GPU work.
     pool = None
@@ -203,110 +368,23 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    cfg = W.config(WORKLOAD)
-    M0 = W.initial_field(cfg)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def timed_steps(fn, k):
-        """k calls of fn, each bracketed by CUDA events on the current stream, L2 flushed between."""
-        tot = 0.0
-        for _ in range(k):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            fn()
-            e1.record()
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot
-
-    # --- FP32 batched form: full macro steps (RK4P start-up inside warm-up, then MPEA).
-    h32 = HMM(cfg, precision=1)
-    lu_batch, _ = h32.stats()
-    plan = h32.plan_report().strip()   # the resident-plan autotuner's timings at init
-    M = torch.from_numpy(M0).cuda()
-    for _ in range(args.warmup):
-        h32.macro_step(M, 1)
-    barrier()
-    with ClockSampler(local_rank) as clk:
-        ms32 = timed_steps(lambda: h32.macro_step(M, 1), args.steps)
-    barrier()
-    ms_max, value = aggregate_ranks(ms32, world, args.steps, lu_batch, dist, "cuda")
-    macro_steps_per_s = args.steps / (ms_max / 1e3)
-
-    # --- dominant kernel: the FP32 micro-batch kernel, timed per launch on its stream.
-    H = torch.empty_like(M)
-    kms = []
-    for _ in range(args.kernel_reps):
-        flush.zero_()
-        h32.micro_batch(M, H)
-        kms.append(h32.stats()[1])
-    k_ms = sum(kms) / len(kms)
-    flops = FLOPS_PER_LU_2D * lu_batch
-    peaks = _peaks()
-    clocks = clk.summary()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    props = torch.cuda.get_device_properties(local_rank)
-    n_sm = props.multi_processor_count
-    alu_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (k_ms / 1e3) / 1e12
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak,
-                "traffic": args.traffic if args.traffic is not None else _traffic_from_profile(),
-                "kernel": "micro_fp32_2d_kernel<3,4,64,58> (shared-memory resident)", "kernel_ms": k_ms,
-                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
-                "hbm_streaming_equivalent": {
-                    "GB_per_s": BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9,
-                    "frac_of_measured_hbm": BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9 / hbm}}
-
-    # --- accuracy of the FP32 form against the FP64 GPU method on the same macro state.
-    h64 = HMM(cfg, precision=0)
-    Mfix = torch.from_numpy(M0).cuda()
-    H32 = h32.micro_batch(Mfix).cpu().numpy()
-    H64 = h64.micro_batch(Mfix).cpu().numpy()
-    rel = float(np.linalg.norm(H32 - H64, axis=0).max() / np.linalg.norm(H64, axis=0).max())
-
-    # --- plain FP64 method: MPEA steps on the same workload (history set so j >= 2).
-    hist = torch.zeros((2, 3, cfg.n_points), dtype=torch.float64, device="cuda")
-    h64.set_state(hist, 2)
-    M64 = torch.from_numpy(M0).cuda()
-    h64.macro_step(M64, 1)
-    k64 = max(1, min(args.steps, args.fp64_steps))
-    ms64 = timed_steps(lambda: h64.macro_step(M64, 1), k64)
-    lu64 = k64 * lu_batch / (ms64 / 1e3)
-    h64.close()
-
-    # --- end to end through the C ABI with host buffers (copies inside the timed region).
-    Mh = torch.from_numpy(M0).pin_memory().numpy()
-    he = HMM(cfg, precision=1)
-    he.macro_step_host(Mh, 3)           # start-up steps + graph capture outside the timing
-    ke = max(1, min(args.steps, args.e2e_steps))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(ke):
-        he.macro_step_host(Mh, 1)
-    e2e_s = time.perf_counter() - t0
-    he.close()
-    e2e = {"value": world * ke * lu_batch / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 3 * cfg.n_points * 8, "d2h_bytes_per_step": 3 * cfg.n_points * 8,
-           "macro_steps_per_s": ke / e2e_s}
-
-    cpu = None
     if pool is not None:
-        oracle_sample(WORKLOAD, 1, args.cpu_workers, pool)   # warm the workers (imports)
-        v, info = oracle_sample(WORKLOAD, args.cpu_boxes_per_worker, args.cpu_workers, pool)
+        pool.map(_warm_worker, range(args.cpu_workers))   # imports, outside every timed sample
+    steps = args.steps if args.steps is not None else WORKLOADS[args.headline]["steps"]
+    head = measure_workload(args.headline, steps, args.warmup, flush, world, dist, pool, args.cpu_workers,
+                            CPU_BOXES.get(args.headline, 2), args.kernel_reps)
+    clocks = head["clocks"]
+    subs = {}
+    if not args.no_sub:
+        for name in SUB_WORKLOADS:
+            if name == args.headline:
+                continue
+            subs[name] = measure_workload(name, WORKLOADS[name]["steps"], max(3, args.warmup), flush, world, dist,
+                                          pool, args.cpu_workers, CPU_BOXES.get(name, 4), args.kernel_reps)
+    if pool is not None:
         pool.close()
-        cpu = {"value": v, "unit": UNIT, "cores": args.cpu_workers, "kind": "oracle",
-               "sample": f"{info['boxes']} of the 16384 micro boxes (full 64^2 x 400 steps each), "
-                         f"{args.cpu_workers} spawned processes, {info['wall_s']:.1f} s wall"}
-    h32.close()
 
     dns = None
     if rank == 0 and not args.no_dns:
@@ -327,22 +405,27 @@ def run_ours(args, rank, world, local_rank):
             dns["cpu_baseline"] = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
+        spec = WORKLOADS[args.headline]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "boxes": cfg.n_points, "micro_nodes": 64,
-                       "micro_steps": 400, "lu_per_step": lu_batch, "precision": "fp32-batched",
-                       "l2": "flushed (256 MB write) between timed steps",
+            "config": {"workload": spec["desc"], "name": args.headline, "boxes": head["boxes"],
+                       "micro_steps": head["micro_steps"], "lu_per_step": head["lu_per_step"],
+                       "precision": "fp32-batched",
+                       "step": "one MPEA macro step (one micro batch over every box + the MPEA update), "
+                               "from a restart state",
+                       "l2": "flushed (256 MB write) between timed steps; the working set is larger than L2",
                        "parallelism": f"replicas x{world}"},
-            "macro_steps_per_s": macro_steps_per_s,
-            "fp64_plain": {"value": lu64, "unit": UNIT, "macro_steps_per_s": k64 / (ms64 / 1e3),
-                           "steps": k64},
-            "speedup_fp32_vs_fp64": value / world / lu64,
-            "fp32_vs_fp64_rel_err": rel,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 3 * args.steps,
-            "plan_autotuner": plan,
+            "macro_steps_per_s": head["macro_steps_per_s"],
+            "fp64_plain": head["fp64_plain"],
+            "speedup_fp32_vs_fp64": head["speedup_fp32_vs_fp64"],
+            "fp32_vs_fp64_rel_err": head["fp32_vs_fp64_rel_err"],
+            "roofline": head["roofline"], "cpu_baseline": head["cpu_baseline"], "e2e": head["e2e"],
+            "clocks": clocks,
+            "gpu_launches": head["gpu_launches_per_step"] * steps,
+            "plan": head["plan"],
+            "workloads": subs,
             "dns": dns,
         }
         print(json.dumps(line), flush=True)
@@ -524,23 +607,28 @@ def run_reference(args, rank, world):
         return
     workers = args.cpu_workers
     pool = mp.get_context("spawn").Pool(workers)
-    oracle_sample(WORKLOAD, 1, workers, pool)
+    pool.map(_warm_worker, range(workers))
+    name = args.headline
+    steps = args.steps if args.steps is not None else WORKLOADS[name]["steps"]
     for _ in range(args.warmup):
-        oracle_sample(WORKLOAD, args.ref_boxes_per_worker, workers, pool)
+        oracle_sample(name, 1, workers, pool)
     tot_lu, tot_s = 0.0, 0.0
-    for _ in range(args.steps):
-        v, info = oracle_sample(WORKLOAD, args.ref_boxes_per_worker, workers, pool)
+    for _ in range(steps):
+        v, info = oracle_sample(name, args.ref_boxes_per_worker, workers, pool)
         tot_lu += info["lu"]
         tot_s += info["wall_s"]
     pool.close()
     value = tot_lu / tot_s
-    sample = (f"each step: {workers * args.ref_boxes_per_worker} of the 16384 micro boxes "
-              f"(full 64^2 x 400 steps), {workers} spawned processes")
+    import workloads as W
+    cfg = W.config(name)
+    sample = (f"each step: {workers * args.ref_boxes_per_worker} of the {cfg.n_points} micro boxes "
+              f"(whole boxes, all {cfg.micro_steps} micro steps), {workers} spawned processes")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "precision": "fp64 oracle"},
+        "data": "synthetic", "config": {"workload": WORKLOADS[name]["desc"], "name": name,
+                                        "precision": "fp64 oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -549,18 +637,19 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed macro steps of the headline workload (default: 1 for the 3D workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--kernel-reps", type=int, default=3)
+    ap.add_argument("--kernel-reps", type=int, default=2)
     ap.add_argument("--cpu-workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--cpu-boxes-per-worker", type=int, default=16)
-    ap.add_argument("--ref-boxes-per-worker", type=int, default=4)
+    ap.add_argument("--ref-boxes-per-worker", type=int, default=1)
+    ap.add_argument("--headline", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="workload of the headline value (the others become sub-objects)")
+    ap.add_argument("--no-sub", action="store_true", help="leave the other workloads' sub-objects out")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
     ap.add_argument("--micro-only", action="store_true",
                     help="time hmm_micro_batch alone (see --workload, --macro-grid, --precision, --variant)")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -581,6 +670,8 @@ def main():
     ap.add_argument("--macro-steps", type=int, default=0,
                     help="with --micro-only: also time this many steady-state macro steps")
     args = ap.parse_args()
+    if args.steps is None and (args.micro_only or args.dns):
+        args.steps = 10
     if args.warmup < 3 and not (args.micro_only or args.dns):
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))

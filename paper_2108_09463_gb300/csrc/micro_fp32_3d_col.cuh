@@ -29,11 +29,13 @@
 //    increasing order); LD is chosen on the host to make the largest residue class
 //    (the number of half-warps) smallest.
 #pragma once
+#include <type_traits>
+
 #include "micro_fp32_3d.cuh"
 
 namespace hmm {
 
-constexpr int kCol3S = 4;            // interior planes per CTA at most
+constexpr int kCol3S = 3;            // interior planes per CTA at most
 constexpr int kCol3MaxTerms = 1;     // separable coefficient terms evaluated in the loop
 constexpr int kCol3MaxThreads = 352; // threads per CTA at most (the launch bound)
 
@@ -412,79 +414,73 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
         const unsigned* rt = rtab + 6 * stage;
         if (cs > 1) cluster_wait(); else __syncthreads();
         float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
-        if (active) {
-          // v at slab plane z (3 components): own planes, the neighbours' planes, or ring zeros
-          auto load_plane = [&](int z, float2* out) {
-            if (z >= 0 && z < S) {
+        // y and x directions of the stencil at slab plane k (local planes only), v0 the
+        // tile's own values there: into Hs
+        auto yx_pass = [&](int k, const float2* v0s, float2* Hs) {
+          const float* Pk = src + k * PV + rowoff;
+          float2 ay[4] = {c02, c02, c02, c02};
+          float ax[5] = {c0f, c0f, c0f, c0f, c0f};
 #pragma unroll
-              for (int c = 0; c < 3; ++c) out[c] = lds2(src + c * cstrV + z * PV + rowoff);
+          for (int t = 0; t < kCol3MaxTerms; ++t) {
+            const float gz = tabv(t, 0, 2 * (zo + k));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ay[q] = fma2(f2(gz, gz), Gy[t][q], ay[q]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) ax[q] = fmaf(gz, Gx[t][q], ax[q]);
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float* P = Pk + c * cstrV;
+            const float2 v0 = v0s[c];
+            // y direction: rows y-3 .. y+3 of plane k, faces y-2|y-1 .. y+1|y+2
+            const float2 vm3 = lds2(P - 3 * LD), vm2 = lds2(P - 2 * LD), vm1 = lds2(P - LD);
+            const float2 vp1 = lds2(P + LD), vp2 = lds2(P + 2 * LD), vp3 = lds2(P + 3 * LD);
+            const float2 Ya = mul2(ay[0], fma2(k27, sub2(vm1, vm2), sub2(vm3, v0)));
+            const float2 Yb = mul2(ay[1], fma2(k27, sub2(v0, vm1), sub2(vm2, vp1)));
+            const float2 Yc = mul2(ay[2], fma2(k27, sub2(vp1, v0), sub2(vm1, vp2)));
+            const float2 Yd = mul2(ay[3], fma2(k27, sub2(vp2, vp1), sub2(v0, vp3)));
+            const float2 h = fma2(k27, sub2(Yc, Yb), sub2(Ya, Yd));
+            // x direction: columns x-3 .. x+4 of the row, faces x-2|x-1 .. x+2|x+3
+            // (a 64-bit load for the one column past R1 keeps the access conflict-free)
+            const float2 L1 = lds2(P - 2), R1 = lds2(P + 2), L2 = lds2(P - 4);
+            const float r2x = lds2(P + 4).x;
+            const float2 g01 = fma2(k27, sub2(shift2(L1, v0), L1), sub2(shift2(L2, L1), v0));
+            const float2 g23 = fma2(k27, sub2(shift2(v0, R1), v0), sub2(shift2(L1, v0), R1));
+            const float g4 = (v0.y - r2x) + 27.f * (R1.y - R1.x);
+            const float2 F01 = mul2(f2(ax[0], ax[1]), g01), F23 = mul2(f2(ax[2], ax[3]), g23);
+            const float F4 = ax[4] * g4;
+            Hs[c] = add2(h, fma2(k27, sub2(F23, shift2(F01, F23)), sub2(F01, f2(F23.y, F4))));
+          }
+        };
+        // One stage on a slab of SS planes (a compile-time count, so that every plane
+        // value lives in registers): the loads of the six planes beyond the slab go out
+        // first, the y and x directions of all own planes (independent of them) follow,
+        // then the z direction walks planes -3 .. SS+2 and each finished plane is updated.
+        auto stage_body = [&](auto ssc) {
+          constexpr int SS = decltype(ssc)::value;
+          float2 rem[6][3];
+#pragma unroll
+          for (int e = 0; e < 6; ++e) {
+            const unsigned b = rt[e];
+            if (b == kRes3Ring) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) rem[e][c] = f2(0.f, 0.f);
             } else {
-              const unsigned b = rt[z < 0 ? z + 3 : z - S + 3];
-              if (b == kRes3Ring) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) out[c] = f2(0.f, 0.f);
-              } else {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) out[c] = col3_remote(b + 4u * (unsigned)(c * cstrV + rowoff));
-              }
+              for (int c = 0; c < 3; ++c) rem[e][c] = col3_remote(b + 4u * (unsigned)(c * cstrV + rowoff));
             }
-          };
-          // y and x directions of the stencil at slab plane k (local planes only), v0 the
-          // tile's own values there: added to Hs
-          auto yx_pass = [&](int k, const float2* v0s, float2* Hs) {
-            const float* Pk = src + k * PV + rowoff;
-            float2 ay[4] = {c02, c02, c02, c02};
-            float ax[5] = {c0f, c0f, c0f, c0f, c0f};
+          }
+          float2 vk[SS][3], Hk[SS][3];
 #pragma unroll
-            for (int t = 0; t < kCol3MaxTerms; ++t) {
-              const float gz = tabv(t, 0, 2 * (zo + k));
+          for (int k = 0; k < SS; ++k) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) ay[q] = fma2(f2(gz, gz), Gy[t][q], ay[q]);
-#pragma unroll
-              for (int q = 0; q < 5; ++q) ax[q] = fmaf(gz, Gx[t][q], ax[q]);
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float* P = Pk + c * cstrV;
-              const float2 v0 = v0s[c];
-              // y direction: rows y-3 .. y+3 of plane k, faces y-2|y-1 .. y+1|y+2
-              const float2 vm3 = lds2(P - 3 * LD), vm2 = lds2(P - 2 * LD), vm1 = lds2(P - LD);
-              const float2 vp1 = lds2(P + LD), vp2 = lds2(P + 2 * LD), vp3 = lds2(P + 3 * LD);
-              const float2 Ya = mul2(ay[0], fma2(k27, sub2(vm1, vm2), sub2(vm3, v0)));
-              const float2 Yb = mul2(ay[1], fma2(k27, sub2(v0, vm1), sub2(vm2, vp1)));
-              const float2 Yc = mul2(ay[2], fma2(k27, sub2(vp1, v0), sub2(vm1, vp2)));
-              const float2 Yd = mul2(ay[3], fma2(k27, sub2(vp2, vp1), sub2(v0, vp3)));
-              float2 h = fma2(k27, sub2(Yc, Yb), sub2(Ya, Yd));
-              // x direction: columns x-3 .. x+4 of the row, faces x-2|x-1 .. x+2|x+3
-              const float2 L1 = lds2(P - 2), R1 = lds2(P + 2), L2 = lds2(P - 4);
-              const float r2x = P[4];
-              const float2 g01 = fma2(k27, sub2(shift2(L1, v0), L1), sub2(shift2(L2, L1), v0));
-              const float2 g23 = fma2(k27, sub2(shift2(v0, R1), v0), sub2(shift2(L1, v0), R1));
-              const float g4 = (v0.y - r2x) + 27.f * (R1.y - R1.x);
-              const float2 F01 = mul2(f2(ax[0], ax[1]), g01), F23 = mul2(f2(ax[2], ax[3]), g23);
-              const float F4 = ax[4] * g4;
-              Hs[c] = add2(h, fma2(k27, sub2(F23, shift2(F01, F23)), sub2(F01, f2(F23.y, F4))));
-            }
-          };
-          // window planes -3 .. -1 (neighbours' or ring) and 0; plane 0's y and x directions
-          // are computed while the neighbours' planes are in flight
-          float2 p0[3], p1[3], p2[3], q0[3], H0[3];
-          load_plane(-3, p0);
-          load_plane(-2, p1);
-          load_plane(-1, p2);
-          load_plane(0, q0);
-          yx_pass(0, q0, H0);
+            for (int c = 0; c < 3; ++c) vk[k][c] = lds2(src + c * cstrV + k * PV + rowoff);
+            yx_pass(k, vk[k], Hk[k]);
+          }
+          auto val = [&](int z, int c) -> float2 { return z < 0 ? rem[z + 3][c] : (z < SS ? vk[z][c] : rem[z - SS + 3][c]); };
           float2 Fa[3], Fb[3], Fc[3];
 #pragma unroll
-          for (int f = -2; f <= kCol3S; ++f) {
-            if (f > S) break;
-            float2 p3[3];
-            if (f == -2) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c) p3[c] = q0[c];
-            } else {
-              load_plane(f + 2, p3);
-            }
+          for (int f = -2; f <= SS; ++f) {
             // z-face between slab planes f and f + 1
             float2 az = c02;
 #pragma unroll
@@ -494,18 +490,16 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
             }
             float2 F[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) F[c] = mul2(az, fma2(k27, sub2(p2[c], p1[c]), sub2(p0[c], p3[c])));
+            for (int c = 0; c < 3; ++c)
+              F[c] = mul2(az, fma2(k27, sub2(val(f + 1, c), val(f, c)), sub2(val(f - 1, c), val(f + 2, c))));
             if (f >= 1) {
               const int k = f - 1;   // plane k is complete in z
-              float2 Hs[3];
-              if (k == 0) {
+              float2 Hs[3], p0[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) Hs[c] = H0[c];
-              } else {
-                yx_pass(k, p0, Hs);
+              for (int c = 0; c < 3; ++c) {
+                Hs[c] = add2(Hk[k][c], fma2(k27, sub2(Fc[c], Fb[c]), sub2(Fa[c], F[c])));
+                p0[c] = vk[k][c];
               }
-#pragma unroll
-              for (int c = 0; c < 3; ++c) Hs[c] = add2(Hs[c], fma2(k27, sub2(Fc[c], Fb[c]), sub2(Fa[c], F[c])));
               const int io = (k * nt + tid) * 2;
               if (stage == 0) {
                 // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
@@ -561,17 +555,19 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
                   part2[c] = fma2(hw, sub2(nv, vh[c]), part2[c]);
                 }
               }
-            }
+          }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               Fa[c] = Fb[c];
               Fb[c] = Fc[c];
               Fc[c] = F[c];
-              p0[c] = p1[c];
-              p1[c] = p2[c];
-              p2[c] = p3[c];
             }
           }
+        };
+        if (active) {
+          if (S == 3) stage_body(std::integral_constant<int, 3>{});
+          else if (S == 2) stage_body(std::integral_constant<int, 2>{});
+          else stage_body(std::integral_constant<int, 1>{});
         }
         if (stage == 1 && om != 0.f) {
           float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};

@@ -1,5 +1,5 @@
 // Instances of the 3D resident kernels (order 4). First the z-column kernel
-// (micro_fp32_3d_col.cuh: boxes up to 32^3, slabs of at most 4 planes, so 7 CTAs for
+// (micro_fp32_3d_col.cuh: boxes from 27^3 to 32^3, slabs of at most 3 planes, so 9 CTAs for
 // 32^3; separable coefficients of at most two terms), then the z-slab kernel's
 // canvases of 16, 24 and 32 nodes per axis with the cluster sizes whose slabs fit one
 // SM (9 CTAs of 3 planes for 32^3), which also serve tabulated coefficients. Larger 3D
