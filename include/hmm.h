@@ -127,10 +127,12 @@ typedef struct {
   int kernel_variant;           /* HMM_FP32_BATCHED kernel: 0 automatic (the
                                    shared-memory-resident kernels when every box
                                    fits them: d = 2, N up to the 8-CTA cluster
-                                   limit; d = 3, order 4, N <= 32; else the generic
-                                   arena kernel), 1 generic, 2 resident            */
-  int micro_stepper;            /* hmm_micro_stepper; RK4P runs on the generic
-                                   kernels (kernel_variant 0 selects them)         */
+                                   limit (HeunP or RK4P); d = 3, order 4, N <= 32,
+                                   HeunP; else the generic arena kernel), 1 generic,
+                                   2 resident                                      */
+  int micro_stepper;            /* hmm_micro_stepper; with RK4P the automatic kernel
+                                   choice takes the resident kernel in 2D and the
+                                   generic kernel in 3D                            */
   int model;                    /* hmm_model                                       */
   int macro_stepper;            /* hmm_macro_stepper (0: MPEA, 1: MPE)             */
   int reserved;                 /* must be zero                                    */

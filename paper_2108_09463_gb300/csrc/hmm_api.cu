@@ -383,7 +383,7 @@ hmm_status tune_resident_plan(HmmHandle* h) {
       int hi = lo;
       while (hi < h->nb && h->boxes[hi].N == N) ++hi;
       const int count = hi - lo;
-      const auto cand = res2d_candidates(N, R, k, nt, smem);
+      const auto cand = res2d_candidates(N, R, k, nt, smem, h->p.micro_stepper);
       lo = hi;
       if (cand.size() < 2) continue;
       const int ns = std::min(count, cap_sample);
@@ -395,7 +395,9 @@ hmm_status tune_resident_plan(HmmHandle* h) {
         std::map<int, std::pair<int, int>> one{{N, cand[c]}};
         Res2dPlan pl;
         std::string why;
-        if (!res2d_make_plan(h->dim, h->boxes.data() + (hi - count), ns, R, k, nt, smem, &pl, &why, &one)) continue;
+        if (!res2d_make_plan(h->dim, h->boxes.data() + (hi - count), ns, R, k, nt, smem, &pl, &why, &one, true,
+                             h->p.micro_stepper))
+          continue;
         if ((int)pl.groups.size() > kQueues) continue;
         if (res2d_prepare(R, &pl, h->num_sms) != cudaSuccess) {
           cudaGetLastError();
@@ -446,7 +448,7 @@ hmm_status tune_resident_plan(HmmHandle* h) {
     // the real plan with the tuned instances
     Res2dPlan pl;
     std::string why;
-    if (!res2d_make_plan(h->dim, h->boxes.data(), h->nb, R, k, nt, smem, &pl, &why, &pick) ||
+    if (!res2d_make_plan(h->dim, h->boxes.data(), h->nb, R, k, nt, smem, &pl, &why, &pick, true, h->p.micro_stepper) ||
         (int)pl.groups.size() > kQueues || res2d_prepare(R, &pl, h->num_sms) != cudaSuccess) {
       cudaGetLastError();
       return HMM_OK;                // keep the heuristic plan
@@ -692,10 +694,11 @@ hmm_status build(HmmHandle* h) {
   // Kernel choice: the resident 2D FP32 kernel when the box fits one SM.
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  std::string why = "the resident kernels need the FP32 form, HeunP and d = 2 or 3";
-  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 && p.micro_stepper == HMM_HEUNP &&
+  std::string why = "the resident kernels need the FP32 form and d = 2 (HeunP or RK4P) or d = 3 (HeunP)";
+  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 &&
+                      (p.micro_stepper == HMM_HEUNP || h->dim == 2) &&
                       res2d_make_plan(h->dim, h->boxes.data(), h->nb, h->radius, h->interp_k, p.n_terms,
-                                      (size_t)optin - 256, &h->plan, &why) &&
+                                      (size_t)optin - 256, &h->plan, &why, nullptr, true, p.micro_stepper) &&
                       (int)h->plan.groups.size() <= kQueues;
   if (p.kernel_variant == 2 && !res_ok) return fail(h, HMM_ERR_INVALID_ARG, why.c_str());
   h->res2d = res_ok && p.kernel_variant != 1;

@@ -21,7 +21,7 @@ const std::vector<ResVariant>& variants(int dim) {
   static const std::vector<ResVariant> all2 = [] {
     std::vector<ResVariant> v;
     int (*getters[])(const ResVariant**) = {res2d_variants_pack, res2d_variants_cluster_a,
-                                            res2d_variants_cluster_b, res2d_variants_any};
+                                            res2d_variants_cluster_b, res2d_variants_any, res2d_variants_rk4};
     for (auto g : getters) {
       const ResVariant* t = nullptr;
       const int n = g(&t);
@@ -77,7 +77,9 @@ bool choose3(int N, int R, int interp_k, int n_terms, size_t budget, bool allow_
 }
 
 ResDims geom(const ResVariant& v, int N, int Sa) {
-  return v.NC > 0 ? res_dims(v.NC, v.R, v.SAC) : res_dims(N, v.R, Sa);
+  ResDims d = v.NC > 0 ? res_dims(v.NC, v.R, v.SAC) : res_dims(N, v.R, Sa);
+  d.rk4 = v.stepper;
+  return d;
 }
 
 // A slab of Sa rows of a box of N nodes under geometry d fits one CTA: shared
@@ -93,13 +95,13 @@ bool cluster_ok(int cs, int Sa, int Ni, int R) {
 
 // The instance and cluster size for a box: the first canvas (table order: growing
 // canvases) that holds it, else the box-stride instance with the smallest cluster.
-bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out) {
+bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out, int stepper) {
   const auto& V = variants(2);
   const int Ni = N - 2 * R;
   int canvases = 0;
   for (int i = 0; i < (int)V.size() && canvases < 3; ++i) {
     const ResVariant& v = V[i];
-    if (v.R != R || v.NC == 0 || v.NC < N) continue;
+    if (v.stepper != stepper || v.R != R || v.NC == 0 || v.NC < N) continue;
     const int Sa = (Ni + v.cs - 1) / v.cs;
     if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
     if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
@@ -109,7 +111,7 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
   }
   for (int i = 0; i < (int)V.size(); ++i) {
     const ResVariant& v = V[i];
-    if (v.R != R || v.NC != 0) continue;
+    if (v.stepper != stepper || v.R != R || v.NC != 0) continue;
     for (int cs = 1; cs <= kResMaxCluster; ++cs) {
       const int Sa = (Ni + cs - 1) / cs;
       if (!cluster_ok(cs, Sa, Ni, R)) continue;
@@ -124,7 +126,8 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
 
 }  // namespace
 
-std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes) {
+std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes,
+                                                  int stepper) {
   // the (instance, cluster size) pairs worth timing for a 2D box of N nodes: the
   // heuristic's own choice first, the three smallest canvases that hold the box (a
   // larger canvas only adds idle threads and shared memory) and the box-stride
@@ -134,11 +137,11 @@ std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, in
   const int Ni = N - 2 * R;
   std::vector<std::pair<int, int>> out;
   int vi = -1, cs = 0;
-  if (choose(N, R, interp_k, n_terms, budget, &vi, &cs)) out.emplace_back(vi, cs);
+  if (choose(N, R, interp_k, n_terms, budget, &vi, &cs, stepper)) out.emplace_back(vi, cs);
   int canvases = 0;
   for (int i = 0; i < (int)V.size() && canvases < 3; ++i) {
     const ResVariant& v = V[i];
-    if (v.R != R || v.NC == 0 || v.NC < N) continue;
+    if (v.stepper != stepper || v.R != R || v.NC == 0 || v.NC < N) continue;
     const int Sa = (Ni + v.cs - 1) / v.cs;
     if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
     if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
@@ -147,7 +150,7 @@ std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, in
   }
   for (int i = 0; i < (int)V.size(); ++i) {
     const ResVariant& v = V[i];
-    if (v.R != R || v.NC != 0) continue;
+    if (v.stepper != stepper || v.R != R || v.NC != 0) continue;
     int found = 0;
     for (int c = 1; c <= kResMaxCluster && found < 2; ++c) {
       const int Sa = (Ni + c - 1) / c;
@@ -170,7 +173,7 @@ bool res3d_plan_uses_col3(const Res2dPlan& plan) {
 
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
                      Res2dPlan* plan, std::string* why, const std::map<int, std::pair<int, int>>* pick,
-                     bool allow_col3) {
+                     bool allow_col3, int stepper) {
   const size_t budget = smem_bytes / sizeof(float);
   const auto& V = variants(2);
   plan->items.clear();
@@ -187,7 +190,7 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
         return true;
       }
     }
-    return choose(N, R, interp_k, n_terms, budget, vi, cs);
+    return choose(N, R, interp_k, n_terms, budget, vi, cs, stepper);
   };
   int i = 0;
   while (i < n) {

@@ -86,6 +86,7 @@ struct ResDims {
   int nf;     // face rows of the x-face array, S + 3 (order 4) or S + 1 (order 2)
   int LDY;    // row stride of the y-face array (>= Ni + 4 or Ni + 2)
   int CPp;    // tiles per row group
+  int rk4;    // 1: the RK4P instance (a third state array and the stage accumulator)
 };
 
 __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
@@ -99,6 +100,7 @@ __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
   d.LDI = res_stride(d.Ni, d.CPp);
   d.nf = S + (R == 3 ? 3 : 1);
   d.LDY = res_stride(d.Ni + (R == 3 ? 4 : 2), d.CPp);
+  d.rk4 = 0;
   return d;
 }
 
@@ -106,14 +108,18 @@ __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
 // canvas of NC nodes per axis and SAC slab rows that holds any box with N <= NC
 // (the strides are then compile-time constants, which keeps the address arithmetic
 // of the time loop out of the registers).
-template <int R, int NC, int SAC>
+template <int R, int NC, int SAC, int ST = 0>
 __host__ __device__ inline ResDims res_geom(int N, int Sa) {
-  return NC > 0 ? res_dims(NC, R, SAC) : res_dims(N, R, Sa);
+  ResDims d = NC > 0 ? res_dims(NC, R, SAC) : res_dims(N, R, Sa);
+  d.rk4 = ST;
+  return d;
 }
 
-// Float offsets of the arrays of one slab, relative to the slab's base.
+// Float offsets of the arrays of one slab, relative to the slab's base. The RK4P
+// instance adds a second stage-state array vC and, in thread order, the per-node
+// accumulator of k1 + 2 k2 + 2 k3 (3 components x TR rows x 2 columns per tile).
 struct ResOffsets {
-  int vA, vB, mi, hi, hw, afx, afy, total;
+  int vA, vB, mi, hi, hw, afx, afy, vC, acc, total;
 };
 
 __host__ __device__ inline ResOffsets res_offsets(const ResDims& d) {
@@ -126,6 +132,13 @@ __host__ __device__ inline ResOffsets res_offsets(const ResDims& d) {
   o.hw = x; x += d.S * d.LDI;
   o.afx = x; x += d.nf * d.LDI;
   o.afy = x; x += d.S * d.LDY;
+  o.vC = 0;
+  o.acc = 0;
+  if (d.rk4) {
+    x = (x + 1) & ~1;
+    o.vC = x; x += 3 * d.rows * d.LD;
+    o.acc = x; x += 3 * kResTR * 2 * (((d.S + kResTR - 1) / kResTR) * d.CPp);
+  }
   o.total = (x + 3) & ~3;   // 16-byte aligned bases
   return o;
 }
@@ -299,17 +312,17 @@ __device__ __forceinline__ void warp_kahan_add(float* kah, int lane, float w, fl
     }
   }
 }
-// Copy the first and last r rows of this CTA's slab of vA (which = 0) or vB
-// (which = 1), all three components, into the halo rows of the neighbouring
+// Copy the first and last r rows of this CTA's slab of vA (which = 0), vB
+// (which = 1) or vC (which = 2, RK4P), all three components, into the halo rows of the neighbouring
 // slabs of the cluster (distributed shared memory). Item geometry from pk[0].
-template <int R, int NC, int SAC>
+template <int R, int NC, int SAC, int ST = 0>
 __device__ __forceinline__ void push_halo(const MicroArgs& a, float* fsm, const PackBox* pk, int which, unsigned rank,
                                           int cs) {
   cg::cluster_group cl = cg::this_cluster();
   const PackBox& p = pk[0];
-  const ResDims d = res_geom<R, NC, SAC>(a.boxes[p.box].N, p.Sa);
+  const ResDims d = res_geom<R, NC, SAC, ST>(a.boxes[p.box].N, p.Sa);
   const ResOffsets of = res_offsets(d);
-  float* V = fsm + p.base + (which ? of.vB : of.vA);
+  float* V = fsm + p.base + (which == 0 ? of.vA : (which == 1 ? of.vB : of.vC));
   const int cstr = d.rows * d.LD, w2 = d.LD / 2, per = 3 * R * w2, S = p.S, Sa = p.Sa;
   for (int e = threadIdx.x; e < 2 * per; e += blockDim.x) {
     const int side = e / per;   // 0: to rank - 1 (its bottom halo), 1: to rank + 1 (its top halo)
@@ -326,7 +339,7 @@ __device__ __forceinline__ void push_halo(const MicroArgs& a, float* fsm, const 
   }
 }
 
-template <int R, int TR, int NC, int SAC>
+template <int R, int TR, int NC, int SAC, int ST = 0>
 __global__ void __launch_bounds__(kResThreads)
 micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
   constexpr int D = 2;
@@ -382,7 +395,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         p.Sa = Sa;
         p.base = o;
         p.warp0 = w0;
-        const ResDims dq = res_geom<R, NC, SAC>(Ni + 2 * R, Sa);
+        const ResDims dq = res_geom<R, NC, SAC, ST>(Ni + 2 * R, Sa);
         p.nwarps = (res_tiles(S, dq.CPp) + 31) / 32;
         w0 += p.nwarps;
         o += res_offsets(dq).total;
@@ -396,7 +409,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       const PackBox p = pk[q];
       const BoxDesc bd = a.boxes[p.box];
       const int N = bd.N;
-      const ResDims d = res_geom<R, NC, SAC>(N, p.Sa);
+      const ResDims d = res_geom<R, NC, SAC, ST>(N, p.Sa);
       const ResOffsets of = res_offsets(d);
       float* base = fsm + p.base;
       float* vA = base + of.vA;
@@ -551,13 +564,13 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
     for (int b = 0; b < npack; ++b)
       if (warp >= pk[b].warp0 && warp < pk[b].warp0 + pk[b].nwarps) q = b;
     bool active = false;
-    ResDims d = res_geom<R, NC, SAC>(2 * R + 2, 1);
+    ResDims d = res_geom<R, NC, SAC, ST>(2 * R + 2, 1);
     int r0 = 0, S = 0, Ni = 1, ii0 = 0, jj0 = 0, obase = 0;
     float dtf = 0.f, csf = 0.f;
     if (q >= 0) {
       const PackBox& p = pk[q];
       const BoxDesc& bd = a.boxes[p.box];
-      d = res_geom<R, NC, SAC>(bd.N, p.Sa);
+      d = res_geom<R, NC, SAC, ST>(bd.N, p.Sa);
       r0 = p.r0;
       S = p.S;
       Ni = bd.N - 2 * R;
@@ -584,113 +597,210 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
     const float2 cs2 = f2(csf, csf);
     const float2 dt2 = f2(dtf, dtf), hdt2 = f2(0.5f * dtf, 0.5f * dtf);
     const float2 half2 = f2(0.5f, 0.5f);
-    __nv_bfloat162 eB[3][TR], vlo[3][TR];
+    if constexpr (ST == 0) {
+      __nv_bfloat162 eB[3][TR], vlo[3][TR];
 #pragma unroll
-    for (int t = 0; t < TR; ++t)
+      for (int t = 0; t < TR; ++t)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        vlo[c][t] = __float2bfloat162_rn(0.f);
-        eB[c][t] = __float2bfloat162_rn(0.f);
-      }
+        for (int c = 0; c < 3; ++c) {
+          vlo[c][t] = __float2bfloat162_rn(0.f);
+          eB[c][t] = __float2bfloat162_rn(0.f);
+        }
 
-    for (int n = 0; n < a.msteps; ++n) {
-      const float om = a.om32[n + 1];
-      if (active) {
-        // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
-        float2 Hs[3][TR];
+      for (int n = 0; n < a.msteps; ++n) {
+        const float om = a.om32[n + 1];
+        if (active) {
+          // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
+          float2 Hs[3][TR];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          tile_stencil<R, TR>(vA + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
+          for (int c = 0; c < 3; ++c)
+            tile_stencil<R, TR>(vA + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
 #pragma unroll
-        for (int t = 0; t < TR; ++t) {
-          const int ii = ii0 + t;
-          if (ii >= S) continue;
-          const int ro = ii * LDI + jj0;
-          const int vo = (ii + R) * LD + j0 + 1;
-          float2 v[3], m[3], H[3], f[3];
+          for (int t = 0; t < TR; ++t) {
+            const int ii = ii0 + t;
+            if (ii >= S) continue;
+            const int ro = ii * LDI + jj0;
+            const int vo = (ii + R) * LD + j0 + 1;
+            float2 v[3], m[3], H[3], f[3];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            v[c] = lds2(vA + c * cstrV + vo);
-            m[c] = add2(lds2(miS + c * cstrI + ro), v[c]);
-            H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * cstrI + ro));
-          }
-          ll_rhs2(m, H, alpha2, f);
+            for (int c = 0; c < 3; ++c) {
+              v[c] = lds2(vA + c * cstrV + vo);
+              m[c] = add2(lds2(miS + c * cstrI + ro), v[c]);
+              H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * cstrI + ro));
+            }
+            ll_rhs2(m, H, alpha2, f);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float2 vb = fma2(dt2, f[c], v[c]);
-            // e_B / 2 = (v + dt k1 - v_B) / 2 (v_B - v is exact): stage 2 adds it to (v_B - v) / 2
-            eB[c][t] = __float22bfloat162_rn(fma2(hdt2, f[c], mul2(half2, sub2(v[c], vb))));
-            if (!col2) vb.y = 0.f;
-            *reinterpret_cast<float2*>(vB + c * cstrV + vo) = vb;
-          }
-        }
-      }
-      __syncthreads();
-      if (cs > 1) {
-        push_halo<R, NC, SAC>(a, fsm, pk, 1, rank, cs);
-        cg::this_cluster().sync();
-      }
-      float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
-      if (active) {
-        // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
-        float2 Hs[3][TR];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          tile_stencil<R, TR>(vB + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
-#pragma unroll
-        for (int t = 0; t < TR; ++t) {
-          const int ii = ii0 + t;
-          if (ii >= S) continue;
-          const int ro = ii * LDI + jj0;
-          const int vo = (ii + R) * LD + j0 + 1;
-          float2 mi[3], m[3], H[3], k2[3], vh[3], dd[3], vt[3], vbo[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            mi[c] = lds2(miS + c * cstrI + ro);
-            vbo[c] = lds2(vB + c * cstrV + vo);
-            m[c] = add2(mi[c], vbo[c]);
-            H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * cstrI + ro));
-          }
-          ll_rhs2(m, H, alpha2, k2);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            vh[c] = lds2(vA + c * cstrV + vo);
-            // dt/2 (k1 + k2) with dt k1 = (v_B - v) + e_B
-            dd[c] = fma2(hdt2, k2[c], fma2(half2, sub2(vbo[c], vh[c]), __bfloat1622float2(eB[c][t])));
-            vt[c] = add2(vh[c], dd[c]);
-          }
-          const float2 hw = lds2(hwS + ro);
-          // s = 2 m_init.vt + |vt|^2; c = -s / (sqrt(1+s)(1+sqrt(1+s)))
-          float2 sdot = mul2(mi[0], vt[0]);
-          sdot = fma2(mi[1], vt[1], sdot);
-          sdot = fma2(mi[2], vt[2], sdot);
-          float2 sq = mul2(vt[0], vt[0]);
-          sq = fma2(vt[1], vt[1], sq);
-          sq = fma2(vt[2], vt[2], sq);
-          const float2 s = fma2(f2(2.f, 2.f), sdot, sq);
-          // (c is a small correction, so the approximate quotient costs nothing measurable)
-          const float rr0 = rsqrtf(1.f + s.x), rr1 = rsqrtf(1.f + s.y);
-          const float2 cf = f2(__fdividef(-s.x * rr0 * rr0, 1.f + rr0), __fdividef(-s.y * rr1 * rr1, 1.f + rr1));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float2 inc = add2(fma2(cf, add2(mi[c], vt[c]), dd[c]), __bfloat1622float2(vlo[c][t]));
-            float2 nh = add2(vh[c], inc);
-            vlo[c][t] = __float22bfloat162_rn(sub2(inc, sub2(nh, vh[c])));
-            if (!col2) nh.y = 0.f;
-            *reinterpret_cast<float2*>(vA + c * cstrV + vo) = nh;
-            // H(W) times the exact change of the stored state (zero in a ring column)
-            part2[c] = fma2(hw, sub2(nh, vh[c]), part2[c]);
+            for (int c = 0; c < 3; ++c) {
+              float2 vb = fma2(dt2, f[c], v[c]);
+              // e_B / 2 = (v + dt k1 - v_B) / 2 (v_B - v is exact): stage 2 adds it to (v_B - v) / 2
+              eB[c][t] = __float22bfloat162_rn(fma2(hdt2, f[c], mul2(half2, sub2(v[c], vb))));
+              if (!col2) vb.y = 0.f;
+              *reinterpret_cast<float2*>(vB + c * cstrV + vo) = vb;
+            }
           }
         }
+        __syncthreads();
+        if (cs > 1) {
+          push_halo<R, NC, SAC, ST>(a, fsm, pk, 1, rank, cs);
+          cg::this_cluster().sync();
+        }
+        float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
+        if (active) {
+          // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
+          float2 Hs[3][TR];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            tile_stencil<R, TR>(vB + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
+#pragma unroll
+          for (int t = 0; t < TR; ++t) {
+            const int ii = ii0 + t;
+            if (ii >= S) continue;
+            const int ro = ii * LDI + jj0;
+            const int vo = (ii + R) * LD + j0 + 1;
+            float2 mi[3], m[3], H[3], k2[3], vh[3], dd[3], vt[3], vbo[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              mi[c] = lds2(miS + c * cstrI + ro);
+              vbo[c] = lds2(vB + c * cstrV + vo);
+              m[c] = add2(mi[c], vbo[c]);
+              H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * cstrI + ro));
+            }
+            ll_rhs2(m, H, alpha2, k2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              vh[c] = lds2(vA + c * cstrV + vo);
+              // dt/2 (k1 + k2) with dt k1 = (v_B - v) + e_B
+              dd[c] = fma2(hdt2, k2[c], fma2(half2, sub2(vbo[c], vh[c]), __bfloat1622float2(eB[c][t])));
+              vt[c] = add2(vh[c], dd[c]);
+            }
+            const float2 hw = lds2(hwS + ro);
+            // s = 2 m_init.vt + |vt|^2; c = -s / (sqrt(1+s)(1+sqrt(1+s)))
+            float2 sdot = mul2(mi[0], vt[0]);
+            sdot = fma2(mi[1], vt[1], sdot);
+            sdot = fma2(mi[2], vt[2], sdot);
+            float2 sq = mul2(vt[0], vt[0]);
+            sq = fma2(vt[1], vt[1], sq);
+            sq = fma2(vt[2], vt[2], sq);
+            const float2 s = fma2(f2(2.f, 2.f), sdot, sq);
+            // (c is a small correction, so the approximate quotient costs nothing measurable)
+            const float rr0 = rsqrtf(1.f + s.x), rr1 = rsqrtf(1.f + s.y);
+            const float2 cf = f2(__fdividef(-s.x * rr0 * rr0, 1.f + rr0), __fdividef(-s.y * rr1 * rr1, 1.f + rr1));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float2 inc = add2(fma2(cf, add2(mi[c], vt[c]), dd[c]), __bfloat1622float2(vlo[c][t]));
+              float2 nh = add2(vh[c], inc);
+              vlo[c][t] = __float22bfloat162_rn(sub2(inc, sub2(nh, vh[c])));
+              if (!col2) nh.y = 0.f;
+              *reinterpret_cast<float2*>(vA + c * cstrV + vo) = nh;
+              // H(W) times the exact change of the stored state (zero in a ring column)
+              part2[c] = fma2(hw, sub2(nh, vh[c]), part2[c]);
+            }
+          }
+        }
+        if (om != 0.f) {
+          float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};
+          warp_kahan_add(kah, lane, om, part);
+        }
+        __syncthreads();
+        if (cs > 1) {
+          push_halo<R, NC, SAC, ST>(a, fsm, pk, 0, rank, cs);
+          cg::this_cluster().sync();
+        }
       }
-      if (om != 0.f) {
-        float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};
-        warp_kahan_add(kah, lane, om, part);
-      }
-      __syncthreads();
-      if (cs > 1) {
-        push_halo<R, NC, SAC>(a, fsm, pk, 0, rank, cs);
-        cg::this_cluster().sync();
+    } else {
+      // RK4P (Section 3.1): k1 = f(v), k2 = f(v + dt/2 k1), k3 = f(v + dt/2 k2),
+      // k4 = f(v + dt k3), v += dt/6 (k1 + 2 k2 + 2 k3 + k4) and the projection, both
+      // written in the perturbation form and compensated as in HeunP (the carried
+      // rounding error of v in bf16). The stage states alternate between vB and vC, so
+      // that a stage reads one while it writes the other; k1 + 2 k2 + 2 k3 accumulates
+      // per node in shared memory in thread order.
+      float* vC = fsm + obase + of.vC;
+      float2* accS = reinterpret_cast<float2*>(fsm + obase + of.acc);
+      const int ntile = res_tiles(S, d.CPp);
+      const int tb = q >= 0 ? (warp - pk[q].warp0) * 32 + lane : 0;   // the tile's index in its slab
+      const float2 sixth2 = f2(dtf / 6.f, dtf / 6.f), two2 = f2(2.f, 2.f);
+      __nv_bfloat162 vlo[3][TR];
+#pragma unroll
+      for (int t = 0; t < TR; ++t)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vlo[c][t] = __float2bfloat162_rn(0.f);
+
+      for (int n = 0; n < a.msteps; ++n) {
+        const float om = a.om32[n + 1];
+        float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+          const float* in = st == 0 ? vA : (st == 2 ? vC : vB);   // this stage's state
+          float* out = st == 1 ? vC : vB;                         // the next stage's state (st < 3)
+          const float2 cnext = st == 2 ? dt2 : hdt2;              // its coefficient of k
+          if (active) {
+            float2 Hs[3][TR];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              tile_stencil<R, TR>(in + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
+#pragma unroll
+            for (int t = 0; t < TR; ++t) {
+              const int ii = ii0 + t;
+              if (ii >= S) continue;
+              const int ro = ii * LDI + jj0;
+              const int vo = (ii + R) * LD + j0 + 1;
+              float2 mi[3], v[3], m[3], H[3], k[3];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                mi[c] = lds2(miS + c * cstrI + ro);
+                v[c] = lds2(vA + c * cstrV + vo);
+                m[c] = add2(mi[c], st == 0 ? v[c] : lds2(in + c * cstrV + vo));
+                H[c] = fma2(Hs[c][t], cs2, lds2(hiS + c * cstrI + ro));
+              }
+              ll_rhs2(m, H, alpha2, k);
+              if (st < 3) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  float2* acc = accS + (c * TR + t) * ntile + tb;
+                  *acc = st == 0 ? k[c] : fma2(two2, k[c], *acc);
+                  float2 u = fma2(cnext, k[c], v[c]);
+                  if (!col2) u.y = 0.f;
+                  *reinterpret_cast<float2*>(out + c * cstrV + vo) = u;
+                }
+              } else {
+                float2 dd[3], vt[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  dd[c] = mul2(sixth2, add2(accS[(c * TR + t) * ntile + tb], k[c]));
+                  vt[c] = add2(v[c], dd[c]);
+                }
+                const float2 hw = lds2(hwS + ro);
+                float2 sdot = mul2(mi[0], vt[0]);
+                sdot = fma2(mi[1], vt[1], sdot);
+                sdot = fma2(mi[2], vt[2], sdot);
+                float2 sq = mul2(vt[0], vt[0]);
+                sq = fma2(vt[1], vt[1], sq);
+                sq = fma2(vt[2], vt[2], sq);
+                const float2 s = fma2(f2(2.f, 2.f), sdot, sq);
+                const float rr0 = rsqrtf(1.f + s.x), rr1 = rsqrtf(1.f + s.y);
+                const float2 cf = f2(__fdividef(-s.x * rr0 * rr0, 1.f + rr0), __fdividef(-s.y * rr1 * rr1, 1.f + rr1));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  const float2 inc = add2(fma2(cf, add2(mi[c], vt[c]), dd[c]), __bfloat1622float2(vlo[c][t]));
+                  float2 nh = add2(v[c], inc);
+                  vlo[c][t] = __float22bfloat162_rn(sub2(inc, sub2(nh, v[c])));
+                  if (!col2) nh.y = 0.f;
+                  *reinterpret_cast<float2*>(vA + c * cstrV + vo) = nh;
+                  part2[c] = fma2(hw, sub2(nh, v[c]), part2[c]);
+                }
+              }
+            }
+          }
+          __syncthreads();
+          if (cs > 1) {
+            push_halo<R, NC, SAC, ST>(a, fsm, pk, st == 3 ? 0 : (st == 1 ? 2 : 1), rank, cs);
+            cg::this_cluster().sync();
+          }
+        }
+        if (om != 0.f) {
+          float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};
+          warp_kahan_add(kah, lane, om, part);
+        }
       }
     }
 
@@ -743,11 +853,13 @@ struct ResVariant {
   int R, NC, SAC, cs;
   void (*fn)(MicroArgs, ResLaunch);
   int TZ;   // 3D: planes per thread tile (0 for 2D; -1: the z-column kernel, cs chosen per box)
+  int stepper;   // micro stepper of the instance: 0 HeunP, 1 RK4P
 };
 
 int res2d_variants_pack(const ResVariant** v);
 int res2d_variants_cluster_a(const ResVariant** v);
 int res2d_variants_cluster_b(const ResVariant** v);
 int res2d_variants_any(const ResVariant** v);
+int res2d_variants_rk4(const ResVariant** v);
 
 }  // namespace hmm

@@ -151,9 +151,34 @@ def test_rk4p_parity(torch_cuda, case, precision):
     assert abs(info["dt"][0] / geo["dt"] - 1) < 1e-12   # the RK4P stability limit, host vs oracle
 
 
-def test_rk4p_rejected_by_resident_kernels(torch_cuda):
+# RK4P on the resident 2D kernel (its own instances: a third state array and the
+# per-node stage accumulator); 3D RK4P runs on the generic kernel.
+RK4P_RESIDENT = {
+    "pack_n24": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=40, micro_stepper=1)),
+    "low_damping_n32": ("c5_sweep", dict(n_macro=(8, 8, 1), box_n=32, micro_steps=40, alpha_micro=0.01,
+                                         micro_stepper=1)),
+    "ragged_n37": ("c2_2d", dict(n_macro=(6, 7, 1), box_n=37, micro_steps=24, micro_stepper=1)),
+    "cluster_n64": ("c2_2d", dict(n_macro=(6, 6, 1), box_n=64, micro_steps=30, micro_stepper=1)),
+    "cluster_n96": ("c5_sweep", dict(n_macro=(5, 5, 1), box_n=96, micro_steps=20, alpha_micro=0.1,
+                                     micro_stepper=1)),
+    "order2": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=40, stencil_order=2, micro_stepper=1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RK4P_RESIDENT))
+def test_rk4p_resident_2d(torch_cuda, case):
+    name, over = RK4P_RESIDENT[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    pts = sorted(set([0, cfg.n_points // 2, cfg.n_points - 1]))
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
+
+
+def test_rk4p_3d_not_resident(torch_cuda):
     from paper_2108_09463_gb300 import HMM, HmmError
-    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=10, micro_stepper=1)
+    cfg = W.config("c4_3d", n_macro=(5, 5, 5), box_n=32, micro_steps=10, micro_stepper=1)
     with pytest.raises(HmmError) as ei:
         HMM(cfg, precision=1, kernel_variant=2)
     assert ei.value.status == 1
