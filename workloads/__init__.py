@@ -140,8 +140,12 @@ def fourier_field(cfg: HMMConfig, seed: int, kmax: int = 4, sigma: float = 0.5,
     norm2 = (ks ** 2).sum(1)
     ks = ks[(norm2 > 0) & (norm2 <= kmax * kmax)]
     amp = sigma / (1.0 + (ks ** 2).sum(1))
-    X = _grid(cfg)
-    shape = X[0].shape
+    # e^{2 pi i k x} per axis, k = -kmax..kmax: the field is the real part of a sum of
+    # products of these (evaluated as d tensor contractions, not one cosine and one
+    # sine per mode and grid point)
+    xs = macro_coords(cfg)
+    E = [np.exp(2j * math.pi * np.outer(np.arange(-kmax, kmax + 1), x)) for x in xs]
+    shape = tuple(len(x) for x in xs)
     for attempt in range(128):
         if attempt and attempt % 16 == 0:
             amp = 0.7 * amp        # a field this rough keeps dipping below min_norm: make it smoother
@@ -149,14 +153,12 @@ def fourier_field(cfg: HMMConfig, seed: int, kmax: int = 4, sigma: float = 0.5,
         B = rng.standard_normal((3, len(ks)))
         mt = np.empty((3,) + shape)
         for c in range(3):
-            acc = np.full(shape, float(offset[c]))
-            for start in range(0, len(ks), 32):
-                kk = ks[start:start + 32]
-                ph = sum(kk[:, a].reshape((-1,) + (1,) * d) * X[a][None] for a in range(d))
-                ph = 2.0 * math.pi * ph
-                acc += np.tensordot(amp[start:start + 32] * A[c, start:start + 32], np.cos(ph), 1)
-                acc += np.tensordot(amp[start:start + 32] * B[c, start:start + 32], np.sin(ph), 1)
-            mt[c] = acc
+            # A cos(2 pi k.x) + B sin(2 pi k.x) = Re((A - iB) e^{2 pi i k.x})
+            Z = np.zeros((2 * kmax + 1,) * d, dtype=complex)
+            Z[tuple((ks + kmax).T)] = amp * (A[c] - 1j * B[c])
+            for a in range(d):
+                Z = np.tensordot(Z, E[a], axes=([0], [0]))
+            mt[c] = float(offset[c]) + Z.real
         nrm = np.sqrt((mt ** 2).sum(0))
         if nrm.min() >= min_norm:
             fourier_field.last_attempt = attempt
