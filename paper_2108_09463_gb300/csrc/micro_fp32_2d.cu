@@ -55,7 +55,10 @@ bool choose3(int N, int R, int interp_k, int n_terms, size_t budget, bool allow_
     if (NT > kCol3MaxThreads || NT < 256) continue;
     const Col3Offsets o = col3_offsets(N, LD, NT);
     if ((size_t)o.total + kResHeaderFloats > budget) continue;
-    if (setup_smem_doubles(3, N, interp_k, n_terms) * 2 > (size_t)3 * kCol3S * N * LD) continue;
+    // the set-up tables and the plane-wise interpolation buffer overlay the stage-state planes
+    if ((setup_smem_doubles(3, N, interp_k, n_terms) + (size_t)3 * (2 * interp_k + 1) * N) * 2 >
+        (size_t)3 * kCol3S * N * LD)
+      continue;
     *vi = i;
     *cs_out = cs;
     return true;

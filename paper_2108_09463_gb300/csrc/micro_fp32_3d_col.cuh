@@ -200,16 +200,42 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
     {
       const int plo = rank == 0 ? 0 : r0 + R;
       const int phi = (int)rank == cs - 1 ? N : r0 + R + S;   // box planes [plo, phi)
-      for (int idx = plo * N * N + tid; idx < phi * N * N; idx += nt) {
-        double P[3];
-        interp_P<D>(a, smr, N, idx, P);
-        const double x = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
-        // 1/sqrt(x): an FP32 estimate refined by two Newton steps in FP64
-        double y = (double)rsqrtf((float)x);
-        y = y * fma(-0.5 * x * y, y, 1.5);
-        y = y * fma(-0.5 * x * y, y, 1.5);
+      // Plane by plane: the neighbourhood contracted along the last axis (smr.part) is
+      // contracted along the first axis at this plane's Lagrange weights into Q (in the
+      // set-up region after its tables), then each node takes the middle axis: 5 FP64 fmas
+      // per component and node instead of 30.
+      const int w = 2 * a.interp_k + 1;
+      double* Q = reinterpret_cast<double*>(vB) + setup_smem_doubles(D, N, a.interp_k, a.n_terms);   // [3][w][N]
+      for (int zb = plo; zb < phi; ++zb) {
+        const double* l0 = smr.lag + (size_t)zb * w;
+        for (int e = tid; e < 3 * w * N; e += nt) {
+          const int c = e / (w * N), r = e - c * w * N, a1 = r / N, jl = r - a1 * N;
+          const double* pc = smr.part + (size_t)c * w * w * N;
+          double acc = 0.0;
+          for (int a0 = 0; a0 < w; ++a0) acc += l0[a0] * pc[((size_t)a0 * w + a1) * N + jl];
+          Q[e] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < N * N; e += nt) {
+          const int j1 = e / N, jl = e - j1 * N;
+          const double* l1 = smr.lag + ((size_t)N + j1) * w;
+          double P[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mi64[c * cap + idx] = P[c] * y;
+          for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int a1 = 0; a1 < w; ++a1) acc += l1[a1] * Q[((size_t)c * w + a1) * N + jl];
+            P[c] = acc;
+          }
+          const double x = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+          // 1/sqrt(x): an FP32 estimate refined by two Newton steps in FP64
+          double y = (double)rsqrtf((float)x);
+          y = y * fma(-0.5 * x * y, y, 1.5);
+          y = y * fma(-0.5 * x * y, y, 1.5);
+          const size_t idx = (size_t)zb * N * N + e;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) mi64[c * cap + idx] = P[c] * y;
+        }
+        __syncthreads();
       }
     }
     if (cs > 1) cg::this_cluster().sync(); else __syncthreads();
