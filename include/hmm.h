@@ -135,7 +135,9 @@ typedef struct {
                                    generic kernel in 3D                            */
   int model;                    /* hmm_model                                       */
   int macro_stepper;            /* hmm_macro_stepper (0: MPEA, 1: MPE)             */
-  int reserved;                 /* must be zero                                    */
+  int tile_rows;                /* resident 2D kernel, rows per thread tile: 0 the
+                                   autotuner chooses (2 or 4 per box size), 2 or 4
+                                   fixes it                                        */
 } hmm_params;
 
 /* Set-up (host only, plus device allocations on the current device).

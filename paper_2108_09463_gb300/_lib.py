@@ -42,7 +42,7 @@ class HmmParams(ctypes.Structure):
                 ("pts_per_eps", c_double), ("mu_over_eps", c_double), ("micro_steps", c_int),
                 ("dt_safety", c_double), ("px", c_int), ("qx", c_int), ("pt", c_int), ("qt", c_int),
                 ("interp_order", c_int), ("stencil_order", c_int), ("precision", c_int),
-                ("kernel_variant", c_int), ("micro_stepper", c_int), ("model", c_int), ("macro_stepper", c_int), ("reserved", c_int)]
+                ("kernel_variant", c_int), ("micro_stepper", c_int), ("model", c_int), ("macro_stepper", c_int), ("tile_rows", c_int)]
 
 
 class HmmDnsParams(ctypes.Structure):
@@ -157,6 +157,7 @@ def make_params(cfg, precision=None, kernel_variant=0):
     p.micro_stepper = int(getattr(cfg, "micro_stepper", 0))
     p.model = int(getattr(cfg, "model", 0))
     p.macro_stepper = int(getattr(cfg, "macro_stepper", 0))
+    p.tile_rows = int(getattr(cfg, "tile_rows", 0))
     return p, keep
 
 

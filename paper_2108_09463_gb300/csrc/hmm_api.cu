@@ -383,7 +383,7 @@ hmm_status tune_resident_plan(HmmHandle* h) {
       int hi = lo;
       while (hi < h->nb && h->boxes[hi].N == N) ++hi;
       const int count = hi - lo;
-      const auto cand = res2d_candidates(N, R, k, nt, smem, h->p.micro_stepper);
+      const auto cand = res2d_candidates(N, R, k, nt, smem, h->p.micro_stepper, h->p.tile_rows);
       lo = hi;
       if (cand.size() < 2) continue;
       const int ns = std::min(count, cap_sample);
@@ -396,7 +396,7 @@ hmm_status tune_resident_plan(HmmHandle* h) {
         Res2dPlan pl;
         std::string why;
         if (!res2d_make_plan(h->dim, h->boxes.data() + (hi - count), ns, R, k, nt, smem, &pl, &why, &one, true,
-                             h->p.micro_stepper))
+                             h->p.micro_stepper, h->p.tile_rows))
           continue;
         if ((int)pl.groups.size() > kQueues) continue;
         if (res2d_prepare(R, &pl, h->num_sms) != cudaSuccess) {
@@ -429,8 +429,8 @@ hmm_status tune_resident_plan(HmmHandle* h) {
         HMM_CUDA(h, cudaEventSynchronize(h->ev1));
         HMM_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         char buf[96];
-        snprintf(buf, sizeof buf, " %s%d x%d %.3f ms", res2d_variant_canvas(cand[c].first) ? "canvas " : "stride ",
-                 res2d_variant_canvas(cand[c].first), cand[c].second, ms / 2);
+        snprintf(buf, sizeof buf, " %s%d x%d tr%d %.3f ms", res2d_variant_canvas(cand[c].first) ? "canvas " : "stride ",
+                 res2d_variant_canvas(cand[c].first), cand[c].second, res2d_variant_rows(cand[c].first), ms / 2);
         line += buf;
         if (ms < best_ms) {
           best_ms = ms;
@@ -448,7 +448,8 @@ hmm_status tune_resident_plan(HmmHandle* h) {
     // the real plan with the tuned instances
     Res2dPlan pl;
     std::string why;
-    if (!res2d_make_plan(h->dim, h->boxes.data(), h->nb, R, k, nt, smem, &pl, &why, &pick, true, h->p.micro_stepper) ||
+    if (!res2d_make_plan(h->dim, h->boxes.data(), h->nb, R, k, nt, smem, &pl, &why, &pick, true, h->p.micro_stepper,
+                         h->p.tile_rows) ||
         (int)pl.groups.size() > kQueues || res2d_prepare(R, &pl, h->num_sms) != cudaSuccess) {
       cudaGetLastError();
       return HMM_OK;                // keep the heuristic plan
@@ -483,7 +484,8 @@ hmm_status tune_resident_plan(HmmHandle* h) {
 hmm_status build(HmmHandle* h) {
   hmm_params& p = h->p;
   if (p.dim < 1 || p.dim > 3) return fail(h, HMM_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
-  if (p.reserved != 0) return fail(h, HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.tile_rows != 0 && p.tile_rows != 2 && p.tile_rows != 4)
+    return fail(h, HMM_ERR_INVALID_ARG, "tile_rows must be 0 (tuned), 2 or 4");
   if (p.macro_stepper != HMM_MPEA && p.macro_stepper != HMM_MPE)
     return fail(h, HMM_ERR_INVALID_ARG, "macro_stepper must be 0 (MPEA) or 1 (MPE)");
   if (p.model != HMM_FIELD_MODEL && p.model != HMM_FLUX_MODEL)
@@ -698,7 +700,8 @@ hmm_status build(HmmHandle* h) {
   const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 &&
                       (p.micro_stepper == HMM_HEUNP || h->dim == 2) &&
                       res2d_make_plan(h->dim, h->boxes.data(), h->nb, h->radius, h->interp_k, p.n_terms,
-                                      (size_t)optin - 256, &h->plan, &why, nullptr, true, p.micro_stepper) &&
+                                      (size_t)optin - 256, &h->plan, &why, nullptr, true, p.micro_stepper,
+                                      p.tile_rows) &&
                       (int)h->plan.groups.size() <= kQueues;
   if (p.kernel_variant == 2 && !res_ok) return fail(h, HMM_ERR_INVALID_ARG, why.c_str());
   h->res2d = res_ok && p.kernel_variant != 1;

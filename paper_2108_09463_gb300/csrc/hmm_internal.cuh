@@ -113,18 +113,22 @@ struct Res2dPlan {
 // heuristic's choice (the autotuner's result), or NULL.
 // allow_col3: 3D boxes may run on the z-column kernel, which evaluates separable
 // coefficient terms in its time loop (false once a face table is set).
-// stepper: the micro stepper (0 HeunP, 1 RK4P: 2D only) whose instances serve the boxes.
+// stepper: the micro stepper (0 HeunP, 1 RK4P: 2D only) whose instances serve the boxes;
+// tr: the heuristic's rows per thread tile (0: 4).
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
                      Res2dPlan* plan, std::string* why,
                      const std::map<int, std::pair<int, int>>* pick = nullptr, bool allow_col3 = true,
-                     int stepper = 0);
+                     int stepper = 0, int tr = 0);
 // True when a 3D plan runs any group on the z-column kernel.
 bool res3d_plan_uses_col3(const Res2dPlan& plan);
 // The (instance, cluster size) pairs that hold a 2D box of N nodes, the
 // heuristic's choice first; the canvas size of an instance (0: box stride).
+// tr: rows per thread tile (0: the instances of every tile height; the heuristic's
+// pick first, which has 4-row tiles)
 std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes,
-                                                  int stepper = 0);
+                                                  int stepper = 0, int tr = 0);
 int res2d_variant_canvas(int vi);
+int res2d_variant_rows(int vi);   // rows per thread tile of a 2D instance
 cudaError_t res2d_prepare(int radius, Res2dPlan* plan, int num_sms);
 int res2d_max_grid(const Res2dPlan& plan);
 size_t res2d_slot_bytes(int nmax);

@@ -21,7 +21,8 @@ const std::vector<ResVariant>& variants(int dim) {
   static const std::vector<ResVariant> all2 = [] {
     std::vector<ResVariant> v;
     int (*getters[])(const ResVariant**) = {res2d_variants_pack, res2d_variants_cluster_a,
-                                            res2d_variants_cluster_b, res2d_variants_any, res2d_variants_rk4};
+                                            res2d_variants_cluster_b, res2d_variants_any, res2d_variants_rk4,
+                                            res2d_variants_tr2};
     for (auto g : getters) {
       const ResVariant* t = nullptr;
       const int n = g(&t);
@@ -82,14 +83,17 @@ bool choose3(int N, int R, int interp_k, int n_terms, size_t budget, bool allow_
 ResDims geom(const ResVariant& v, int N, int Sa) {
   ResDims d = v.NC > 0 ? res_dims(v.NC, v.R, v.SAC) : res_dims(N, v.R, Sa);
   d.rk4 = v.stepper;
+  d.TR = v.tr > 0 ? v.tr : kResTR;
   return d;
 }
+
+int tile_rows(const ResVariant& v) { return v.tr > 0 ? v.tr : kResTR; }
 
 // A slab of Sa rows of a box of N nodes under geometry d fits one CTA: shared
 // memory (with the header), threads, and the set-up tables inside the vB region.
 bool slab_fits(const ResDims& d, int N, int Sa, int interp_k, int n_terms, size_t budget_floats) {
   return (size_t)res_offsets(d).total + kResHeaderFloats <= budget_floats &&
-         (res_tiles(Sa, d.CPp) + 31) / 32 * 32 <= kResThreads && res_setup_fits(d, N, interp_k, n_terms);
+         (res_tiles(Sa, d.CPp, d.TR) + 31) / 32 * 32 <= kResThreads && res_setup_fits(d, N, interp_k, n_terms);
 }
 
 bool cluster_ok(int cs, int Sa, int Ni, int R) {
@@ -98,13 +102,14 @@ bool cluster_ok(int cs, int Sa, int Ni, int R) {
 
 // The instance and cluster size for a box: the first canvas (table order: growing
 // canvases) that holds it, else the box-stride instance with the smallest cluster.
-bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out, int stepper) {
+bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int* cs_out, int stepper, int tr) {
+  if (tr <= 0) tr = kResTR;
   const auto& V = variants(2);
   const int Ni = N - 2 * R;
   int canvases = 0;
   for (int i = 0; i < (int)V.size() && canvases < 3; ++i) {
     const ResVariant& v = V[i];
-    if (v.stepper != stepper || v.R != R || v.NC == 0 || v.NC < N) continue;
+    if (v.stepper != stepper || tile_rows(v) != tr || v.R != R || v.NC == 0 || v.NC < N) continue;
     const int Sa = (Ni + v.cs - 1) / v.cs;
     if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
     if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
@@ -114,7 +119,8 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
   }
   for (int i = 0; i < (int)V.size(); ++i) {
     const ResVariant& v = V[i];
-    if (v.stepper != stepper || v.R != R || v.NC != 0) continue;
+    if (v.stepper != stepper || tile_rows(v) != kResTR || v.R != R || v.NC != 0) continue;
+    if (tr != kResTR) continue;   // the box-stride instances have 4-row tiles
     for (int cs = 1; cs <= kResMaxCluster; ++cs) {
       const int Sa = (Ni + cs - 1) / cs;
       if (!cluster_ok(cs, Sa, Ni, R)) continue;
@@ -130,7 +136,7 @@ bool choose(int N, int R, int interp_k, int n_terms, size_t budget, int* vi, int
 }  // namespace
 
 std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, int n_terms, size_t smem_bytes,
-                                                  int stepper) {
+                                                  int stepper, int tr) {
   // the (instance, cluster size) pairs worth timing for a 2D box of N nodes: the
   // heuristic's own choice first, the three smallest canvases that hold the box (a
   // larger canvas only adds idle threads and shared memory) and the box-stride
@@ -140,20 +146,25 @@ std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, in
   const int Ni = N - 2 * R;
   std::vector<std::pair<int, int>> out;
   int vi = -1, cs = 0;
-  if (choose(N, R, interp_k, n_terms, budget, &vi, &cs, stepper)) out.emplace_back(vi, cs);
-  int canvases = 0;
-  for (int i = 0; i < (int)V.size() && canvases < 3; ++i) {
-    const ResVariant& v = V[i];
-    if (v.stepper != stepper || v.R != R || v.NC == 0 || v.NC < N) continue;
-    const int Sa = (Ni + v.cs - 1) / v.cs;
-    if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
-    if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
-    ++canvases;
-    if (std::find(out.begin(), out.end(), std::make_pair(i, v.cs)) == out.end()) out.emplace_back(i, v.cs);
+  if (choose(N, R, interp_k, n_terms, budget, &vi, &cs, stepper, tr)) out.emplace_back(vi, cs);
+  // the three smallest canvases of 4-row tiles and the two smallest of 2-row tiles
+  for (int trc : {kResTR, 2}) {
+    if (tr > 0 && trc != tr) continue;
+    int canvases = 0;
+    for (int i = 0; i < (int)V.size() && canvases < (trc == kResTR ? 3 : 2); ++i) {
+      const ResVariant& v = V[i];
+      if (v.stepper != stepper || tile_rows(v) != trc || v.R != R || v.NC == 0 || v.NC < N) continue;
+      const int Sa = (Ni + v.cs - 1) / v.cs;
+      if (Sa > v.SAC || !cluster_ok(v.cs, Sa, Ni, R)) continue;
+      if (!slab_fits(geom(v, N, Sa), N, Sa, interp_k, n_terms, budget)) continue;
+      ++canvases;
+      if (std::find(out.begin(), out.end(), std::make_pair(i, v.cs)) == out.end()) out.emplace_back(i, v.cs);
+    }
   }
   for (int i = 0; i < (int)V.size(); ++i) {
     const ResVariant& v = V[i];
-    if (v.stepper != stepper || v.R != R || v.NC != 0) continue;
+    if (v.stepper != stepper || tile_rows(v) != kResTR || v.R != R || v.NC != 0) continue;
+    if (tr > 0 && tr != kResTR) continue;
     int found = 0;
     for (int c = 1; c <= kResMaxCluster && found < 2; ++c) {
       const int Sa = (Ni + c - 1) / c;
@@ -166,6 +177,7 @@ std::vector<std::pair<int, int>> res2d_candidates(int N, int R, int interp_k, in
 }
 
 int res2d_variant_canvas(int vi) { return variants(2)[vi].NC; }
+int res2d_variant_rows(int vi) { return tile_rows(variants(2)[vi]); }
 
 bool res3d_plan_uses_col3(const Res2dPlan& plan) {
   if (plan.dim != 3) return false;
@@ -176,7 +188,7 @@ bool res3d_plan_uses_col3(const Res2dPlan& plan) {
 
 bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, int n_terms, size_t smem_bytes,
                      Res2dPlan* plan, std::string* why, const std::map<int, std::pair<int, int>>* pick,
-                     bool allow_col3, int stepper) {
+                     bool allow_col3, int stepper, int tr) {
   const size_t budget = smem_bytes / sizeof(float);
   const auto& V = variants(2);
   plan->items.clear();
@@ -193,7 +205,7 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
         return true;
       }
     }
-    return choose(N, R, interp_k, n_terms, budget, vi, cs, stepper);
+    return choose(N, R, interp_k, n_terms, budget, vi, cs, stepper, tr);
   };
   int i = 0;
   while (i < n) {
@@ -234,7 +246,7 @@ bool res2d_make_plan(int dim, const BoxDesc* boxes, int n, int R, int interp_k, 
         if (!choose_for(N, &vj, &csj) || vj != vi || csj != 1) break;
         const ResDims dq = geom(V[vi], N, Ni);
         const size_t f = res_offsets(dq).total;
-        const int w = (res_tiles(Ni, dq.CPp) + 31) / 32;
+        const int w = (res_tiles(Ni, dq.CPp, dq.TR) + 31) / 32;
         if (k > 0 && (floats + f > budget || (warps + w) * 32 > kResThreads)) break;
         floats += f;
         warps += w;

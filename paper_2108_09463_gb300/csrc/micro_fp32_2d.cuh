@@ -87,6 +87,7 @@ struct ResDims {
   int LDY;    // row stride of the y-face array (>= Ni + 4 or Ni + 2)
   int CPp;    // tiles per row group
   int rk4;    // 1: the RK4P instance (a third state array and the stage accumulator)
+  int TR;     // rows per thread tile of the instance
 };
 
 __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
@@ -101,6 +102,7 @@ __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
   d.nf = S + (R == 3 ? 3 : 1);
   d.LDY = res_stride(d.Ni + (R == 3 ? 4 : 2), d.CPp);
   d.rk4 = 0;
+  d.TR = kResTR;
   return d;
 }
 
@@ -108,10 +110,11 @@ __host__ __device__ inline ResDims res_dims(int N, int R, int S) {
 // canvas of NC nodes per axis and SAC slab rows that holds any box with N <= NC
 // (the strides are then compile-time constants, which keeps the address arithmetic
 // of the time loop out of the registers).
-template <int R, int NC, int SAC, int ST = 0>
+template <int R, int NC, int SAC, int ST = 0, int TRr = kResTR>
 __host__ __device__ inline ResDims res_geom(int N, int Sa) {
   ResDims d = NC > 0 ? res_dims(NC, R, SAC) : res_dims(N, R, Sa);
   d.rk4 = ST;
+  d.TR = TRr;
   return d;
 }
 
@@ -137,7 +140,7 @@ __host__ __device__ inline ResOffsets res_offsets(const ResDims& d) {
   if (d.rk4) {
     x = (x + 1) & ~1;
     o.vC = x; x += 3 * d.rows * d.LD;
-    o.acc = x; x += 3 * kResTR * 2 * (((d.S + kResTR - 1) / kResTR) * d.CPp);
+    o.acc = x; x += 3 * d.TR * 2 * (((d.S + d.TR - 1) / d.TR) * d.CPp);
   }
   o.total = (x + 3) & ~3;   // 16-byte aligned bases
   return o;
@@ -160,7 +163,7 @@ constexpr int kResHeaderFloats =
     ((2 * (kResRedDoubles + kResCsumDoubles) + (int)(kResMaxPack * sizeof(PackBox) / 4) + 6 * (kResThreads / 32)) + 3) & ~3;
 
 // Tiles (threads) of a slab of S rows with CPp tiles per row group.
-__host__ __device__ inline int res_tiles(int S, int CPp) { return ((S + kResTR - 1) / kResTR) * CPp; }
+__host__ __device__ inline int res_tiles(int S, int CPp, int TR = kResTR) { return ((S + TR - 1) / TR) * CPp; }
 
 // Set-up tables (FP64) overlay the slab's vB region while the slab is being set up.
 __host__ __device__ inline bool res_setup_fits(const ResDims& d, int N, int interp_k, int n_terms) {
@@ -315,12 +318,12 @@ __device__ __forceinline__ void warp_kahan_add(float* kah, int lane, float w, fl
 // Copy the first and last r rows of this CTA's slab of vA (which = 0), vB
 // (which = 1) or vC (which = 2, RK4P), all three components, into the halo rows of the neighbouring
 // slabs of the cluster (distributed shared memory). Item geometry from pk[0].
-template <int R, int NC, int SAC, int ST = 0>
+template <int R, int NC, int SAC, int ST = 0, int TR = kResTR>
 __device__ __forceinline__ void push_halo(const MicroArgs& a, float* fsm, const PackBox* pk, int which, unsigned rank,
                                           int cs) {
   cg::cluster_group cl = cg::this_cluster();
   const PackBox& p = pk[0];
-  const ResDims d = res_geom<R, NC, SAC, ST>(a.boxes[p.box].N, p.Sa);
+  const ResDims d = res_geom<R, NC, SAC, ST, TR>(a.boxes[p.box].N, p.Sa);
   const ResOffsets of = res_offsets(d);
   float* V = fsm + p.base + (which == 0 ? of.vA : (which == 1 ? of.vB : of.vC));
   const int cstr = d.rows * d.LD, w2 = d.LD / 2, per = 3 * R * w2, S = p.S, Sa = p.Sa;
@@ -395,8 +398,8 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         p.Sa = Sa;
         p.base = o;
         p.warp0 = w0;
-        const ResDims dq = res_geom<R, NC, SAC, ST>(Ni + 2 * R, Sa);
-        p.nwarps = (res_tiles(S, dq.CPp) + 31) / 32;
+        const ResDims dq = res_geom<R, NC, SAC, ST, TR>(Ni + 2 * R, Sa);
+        p.nwarps = (res_tiles(S, dq.CPp, TR) + 31) / 32;
         w0 += p.nwarps;
         o += res_offsets(dq).total;
       }
@@ -409,7 +412,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       const PackBox p = pk[q];
       const BoxDesc bd = a.boxes[p.box];
       const int N = bd.N;
-      const ResDims d = res_geom<R, NC, SAC, ST>(N, p.Sa);
+      const ResDims d = res_geom<R, NC, SAC, ST, TR>(N, p.Sa);
       const ResOffsets of = res_offsets(d);
       float* base = fsm + p.base;
       float* vA = base + of.vA;
@@ -564,13 +567,13 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
     for (int b = 0; b < npack; ++b)
       if (warp >= pk[b].warp0 && warp < pk[b].warp0 + pk[b].nwarps) q = b;
     bool active = false;
-    ResDims d = res_geom<R, NC, SAC, ST>(2 * R + 2, 1);
+    ResDims d = res_geom<R, NC, SAC, ST, TR>(2 * R + 2, 1);
     int r0 = 0, S = 0, Ni = 1, ii0 = 0, jj0 = 0, obase = 0;
     float dtf = 0.f, csf = 0.f;
     if (q >= 0) {
       const PackBox& p = pk[q];
       const BoxDesc& bd = a.boxes[p.box];
-      d = res_geom<R, NC, SAC, ST>(bd.N, p.Sa);
+      d = res_geom<R, NC, SAC, ST, TR>(bd.N, p.Sa);
       r0 = p.r0;
       S = p.S;
       Ni = bd.N - 2 * R;
@@ -578,7 +581,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       const int t = (warp - p.warp0) * 32 + lane;
       ii0 = (t / d.CPp) * TR;          // row within the slab
       jj0 = 2 * (t % d.CPp);
-      active = t < res_tiles(S, d.CPp) && jj0 < Ni;
+      active = t < res_tiles(S, d.CPp, TR) && jj0 < Ni;
       dtf = (float)bd.dt;
       csf = (float)(R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx));
     }
@@ -641,7 +644,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         }
         __syncthreads();
         if (cs > 1) {
-          push_halo<R, NC, SAC, ST>(a, fsm, pk, 1, rank, cs);
+          push_halo<R, NC, SAC, ST, TR>(a, fsm, pk, 1, rank, cs);
           cg::this_cluster().sync();
         }
         float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
@@ -703,7 +706,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
         }
         __syncthreads();
         if (cs > 1) {
-          push_halo<R, NC, SAC, ST>(a, fsm, pk, 0, rank, cs);
+          push_halo<R, NC, SAC, ST, TR>(a, fsm, pk, 0, rank, cs);
           cg::this_cluster().sync();
         }
       }
@@ -716,7 +719,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       // per node in shared memory in thread order.
       float* vC = fsm + obase + of.vC;
       float2* accS = reinterpret_cast<float2*>(fsm + obase + of.acc);
-      const int ntile = res_tiles(S, d.CPp);
+      const int ntile = res_tiles(S, d.CPp, TR);
       const int tb = q >= 0 ? (warp - pk[q].warp0) * 32 + lane : 0;   // the tile's index in its slab
       const float2 sixth2 = f2(dtf / 6.f, dtf / 6.f), two2 = f2(2.f, 2.f);
       __nv_bfloat162 vlo[3][TR];
@@ -793,7 +796,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
           }
           __syncthreads();
           if (cs > 1) {
-            push_halo<R, NC, SAC, ST>(a, fsm, pk, st == 3 ? 0 : (st == 1 ? 2 : 1), rank, cs);
+            push_halo<R, NC, SAC, ST, TR>(a, fsm, pk, st == 3 ? 0 : (st == 1 ? 2 : 1), rank, cs);
             cg::this_cluster().sync();
           }
         }
@@ -854,6 +857,7 @@ struct ResVariant {
   void (*fn)(MicroArgs, ResLaunch);
   int TZ;   // 3D: planes per thread tile (0 for 2D; -1: the z-column kernel, cs chosen per box)
   int stepper;   // micro stepper of the instance: 0 HeunP, 1 RK4P
+  int tr;        // 2D: rows per thread tile (0: kResTR)
 };
 
 int res2d_variants_pack(const ResVariant** v);
@@ -861,5 +865,6 @@ int res2d_variants_cluster_a(const ResVariant** v);
 int res2d_variants_cluster_b(const ResVariant** v);
 int res2d_variants_any(const ResVariant** v);
 int res2d_variants_rk4(const ResVariant** v);
+int res2d_variants_tr2(const ResVariant** v);
 
 }  // namespace hmm

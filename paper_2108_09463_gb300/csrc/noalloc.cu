@@ -119,7 +119,8 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point runs the FP32 form only");
   if (p.eps_field || p.box_n_field)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point needs uniform eps and N");
-  if (p.reserved != 0) return noalloc_fail(HMM_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (p.tile_rows != 0 && p.tile_rows != 2 && p.tile_rows != 4)
+    return noalloc_fail(HMM_ERR_INVALID_ARG, "tile_rows must be 0, 2 or 4");
   if (p.macro_stepper != HMM_MPEA && p.macro_stepper != HMM_MPE)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "macro_stepper must be 0 (MPEA) or 1 (MPE)");
   if (p.model != HMM_FIELD_MODEL) return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free batch runs the field model");

@@ -318,6 +318,29 @@ def test_resident_3d_kernel(torch_cuda, case):
     assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
 
 
+# 2-row thread tiles (tile_rows = 2: twice the threads per slab of the 4-row tiles), which
+# the plan autotuner may pick per box size: packs, a ragged box, and boxes on clusters of
+# 3 and 5 CTAs.
+TR2 = {
+    "pack_n24": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=40)),
+    "ragged_n37": ("c2_2d", dict(n_macro=(6, 7, 1), box_n=37, micro_steps=24)),
+    "pack_n48": ("c5_sweep", dict(n_macro=(6, 6, 1), box_n=48, micro_steps=30)),
+    "cluster3_n64": ("c2_2d", dict(n_macro=(6, 6, 1), box_n=64, micro_steps=30)),
+    "cluster5_n96": ("c5_sweep", dict(n_macro=(5, 5, 1), box_n=96, micro_steps=20, alpha_micro=0.1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(TR2))
+def test_resident_2d_two_row_tiles(torch_cuda, case):
+    name, over = TR2[case]
+    cfg = W.config(name, **over).replace(tile_rows=2)
+    M0 = W.initial_field(cfg)
+    Hg, _ = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    pts = sorted(set([0, cfg.n_points // 2, cfg.n_points - 1]))
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
+
+
 def test_resident_2d_kernel_uneven_boxes(torch_cuda):
     cfg = _uneven_small()
     M0 = W.initial_field(cfg)

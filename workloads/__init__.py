@@ -68,6 +68,7 @@ class HMMConfig:
     model                    0: field model (H_avg), 1: flux model (F_avg at staggered
                              points, its macro divergence in place of H_avg; Section 2.2)
     macro_stepper            0: MPEA, 1: MPE (Section 3.1) for the macro steps
+    tile_rows                resident 2D kernel: rows per thread tile (0 tuned, 2 or 4)
     coef_fn                  a coefficient that is not a sum of separable terms:
                              coef_fn(X, eps) -> a at the points X (a list of d
                              coordinate arrays); replaces c0 + terms when set
@@ -98,6 +99,7 @@ class HMMConfig:
     micro_stepper: int = 0
     model: int = 0
     macro_stepper: int = 0
+    tile_rows: int = 0
     coef_fn: Optional[Callable] = None
     name: str = ""
 
