@@ -121,27 +121,37 @@ __host__ __device__ inline ResDims res_geom(int N, int Sa) {
 // Float offsets of the arrays of one slab, relative to the slab's base. The RK4P
 // instance adds a second stage-state array vC and, in thread order, the per-node
 // accumulator of k1 + 2 k2 + 2 k3 (3 components x TR rows x 2 columns per tile).
+//
+// The stencil reads the state arrays and the face coefficients without clamping its
+// rows: the tiles of a ragged last tile row read up to TR - 1 rows past the slab, whose
+// values only reach the rows it discards. So those arrays come first (vA, vB, vC, afx,
+// afy), each followed by arrays that absorb the overrun, and the slab is padded where
+// the rest of it is shorter than the overrun of the array before.
 struct ResOffsets {
   int vA, vB, mi, hi, hw, afx, afy, vC, acc, total;
 };
 
 __host__ __device__ inline ResOffsets res_offsets(const ResDims& d) {
   ResOffsets o;
-  int x = 0;
-  o.vA = x; x += 3 * d.rows * d.LD;
-  o.vB = x; x += 3 * d.rows * d.LD;
-  o.mi = x; x += 3 * d.S * d.LDI;
-  o.hi = x; x += 3 * d.S * d.LDI;
-  o.hw = x; x += d.S * d.LDI;
-  o.afx = x; x += d.nf * d.LDI;
-  o.afy = x; x += d.S * d.LDY;
+  int x = 0, need = 0;
+  const int over = ((d.S + d.TR - 1) / d.TR) * d.TR - d.S + 1;   // rows past the end, + column overshoot
+  auto place = [&](int* off, int size, int stride) {
+    *off = x;
+    x += size;
+    if (stride > 0) need = need > x + over * stride + 8 ? need : x + over * stride + 8;
+  };
   o.vC = 0;
   o.acc = 0;
-  if (d.rk4) {
-    x = (x + 1) & ~1;
-    o.vC = x; x += 3 * d.rows * d.LD;
-    o.acc = x; x += 3 * d.TR * 2 * (((d.S + d.TR - 1) / d.TR) * d.CPp);
-  }
+  place(&o.vA, 3 * d.rows * d.LD, d.LD);
+  place(&o.vB, 3 * d.rows * d.LD, d.LD);
+  if (d.rk4) place(&o.vC, 3 * d.rows * d.LD, d.LD);
+  place(&o.afx, d.nf * d.LDI, d.LDI);
+  place(&o.afy, d.S * d.LDY, d.LDY);
+  place(&o.mi, 3 * d.S * d.LDI, 0);
+  place(&o.hi, 3 * d.S * d.LDI, 0);
+  place(&o.hw, d.S * d.LDI, 0);
+  if (d.rk4) place(&o.acc, 3 * d.TR * 2 * (((d.S + d.TR - 1) / d.TR) * d.CPp), 0);
+  x = x > need ? x : need;
   o.total = (x + 3) & ~3;   // 16-byte aligned bases
   return o;
 }
@@ -164,6 +174,13 @@ constexpr int kResHeaderFloats =
 
 // Tiles (threads) of a slab of S rows with CPp tiles per row group.
 __host__ __device__ inline int res_tiles(int S, int CPp, int TR = kResTR) { return ((S + TR - 1) / TR) * CPp; }
+
+// Whether a box of Ni interior nodes per row, laid out CPp tiles per row group, can
+// take its right-hand y faces from the next two lanes: the row group fills a half or
+// a whole warp, and the two lanes after its last interior tile are in it.
+__host__ __device__ inline bool res_yshfl_ok(int Ni, int CPp) {
+  return (CPp == 16 || CPp == 32) && (Ni + 1) / 2 <= CPp - 2;
+}
 
 // Set-up tables (FP64) overlay the slab's vB region while the slab is being set up.
 __host__ __device__ inline bool res_setup_fits(const ResDims& d, int N, int interp_k, int n_terms) {
@@ -206,16 +223,23 @@ __device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cas
 // Stencil of one component at the thread's TR x 2 tile. V: the component plane of
 // vA or vB (row stride LD, column j at offset j + 1). Result H (without the
 // 1/dx^2 or 1/(24 dx)^2 factor) per row.
+//
+// yshfl (warp-uniform): every lane of the warp runs this, a row group of tiles lies in
+// consecutive lanes with at least two lanes of slack after its last interior tile
+// (res_yshfl_ok), and each lane computes only the y-face fluxes on the left of its two
+// nodes; the faces on the right are the next lanes' left faces, taken by shuffles.
+// Otherwise each lane computes all the y faces it needs (2.5 per node).
 template <int R, int TR>
-__device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD, int N, int i0, int j0,
-                                             const float* __restrict__ afx, int LDI, int nf, int jj0,
-                                             const float* __restrict__ afy, int LDY, int ii0, int Ni,
+__device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD, int i0, int j0,
+                                             const float* __restrict__ afx, int LDI, int jj0,
+                                             const float* __restrict__ afy, int LDY, int ii0, bool yshfl,
                                              float2* H) {
   // x direction (rows): a rolling window over the rows and over the face fluxes.
   // Each node combines its four fluxes as (F_t - F_{t+3}) + 27 (F_{t+2} - F_{t+1}):
   // the two differences of neighbouring fluxes cancel with little rounding.
-  auto ld = [&](int k) { return lds2(V + min(i0 - R + k, N - 1) * LD + j0 + 1); };
-  auto axf = [&](int f) { return lds2(afx + min(ii0 + f, nf - 1) * LDI + jj0); };
+  // (rows are not clamped: the slab layout absorbs the ragged tile row's overrun)
+  auto ld = [&](int k) { return lds2(V + (i0 - R + k) * LD + j0 + 1); };
+  auto axf = [&](int f) { return lds2(afx + (ii0 + f) * LDI + jj0); };
   const float2 k27 = f2(27.f, 27.f);
   float2 Cc[TR];   // centre values of the tile rows (reused by the y direction)
   if (R == 3) {
@@ -247,13 +271,39 @@ __device__ __forceinline__ void tile_stencil(const float* __restrict__ V, int LD
     }
   }
   // y direction (columns), faces between columns, row by row
+  if (yshfl) {
+    constexpr unsigned kAll = 0xffffffffu;
+#pragma unroll
+    for (int t = 0; t < TR; ++t) {
+      const float* row = V + (i0 + t) * LD + j0 + 1;
+      const float2 C = Cc[t];
+      const float2 a01 = lds2(afy + (ii0 + t) * LDY + jj0);
+      if (R == 3) {
+        // this lane's faces j0-2, j0-1; faces j0, j0+1 from lane + 1 and j0+2 from lane + 2
+        const float2 L1 = lds2(row - 2);
+        const float l2 = row[-3];
+        const float2 F01 = mul2(a01, fma2(k27, sub2(shift2(L1, C), L1), sub2(f2(l2, L1.x), C)));
+        const float2 F23 = f2(__shfl_down_sync(kAll, F01.x, 1), __shfl_down_sync(kAll, F01.y, 1));
+        const float F4 = __shfl_down_sync(kAll, F01.x, 2);
+        const float2 hy = fma2(k27, sub2(F23, shift2(F01, F23)), sub2(F01, f2(F23.y, F4)));
+        H[t] = add2(H[t], hy);
+      } else {
+        // this lane's faces j0-1|j0 and j0|j0+1; face j0+1|j0+2 from lane + 1
+        const float l1 = row[-1];
+        const float2 F01 = mul2(a01, sub2(C, f2(l1, C.x)));
+        const float F2 = __shfl_down_sync(kAll, F01.x, 1);
+        H[t] = add2(H[t], sub2(f2(F01.y, F2), F01));
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int t = 0; t < TR; ++t) {
-    const float* row = V + min(i0 + t, N - 1) * LD + j0 + 1;
+    const float* row = V + (i0 + t) * LD + j0 + 1;
     const float2 C = Cc[t];
     const float2 L1 = lds2(row - 2);
     const float2 R1 = lds2(row + 2);
-    const float* ay = afy + min(ii0 + t, Ni - 1) * LDY + jj0;
+    const float* ay = afy + (ii0 + t) * LDY + jj0;
     if (R == 3) {
       const float2 L2 = lds2(row - 4);
       const float r2x = row[4];
@@ -566,7 +616,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
     int q = -1;
     for (int b = 0; b < npack; ++b)
       if (warp >= pk[b].warp0 && warp < pk[b].warp0 + pk[b].nwarps) q = b;
-    bool active = false;
+    bool active = false, yshfl = false;
     ResDims d = res_geom<R, NC, SAC, ST, TR>(2 * R + 2, 1);
     int r0 = 0, S = 0, Ni = 1, ii0 = 0, jj0 = 0, obase = 0;
     float dtf = 0.f, csf = 0.f;
@@ -582,11 +632,17 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
       ii0 = (t / d.CPp) * TR;          // row within the slab
       jj0 = 2 * (t % d.CPp);
       active = t < res_tiles(S, d.CPp, TR) && jj0 < Ni;
+      yshfl = res_yshfl_ok(Ni, d.CPp);
+      // lanes past the needed ones run the stencil on the last needed column and tile row
+      if (yshfl) {
+        jj0 = min(jj0, 2 * ((Ni + 1) / 2) + (R == 3 ? 2 : 0));
+        ii0 = min(ii0, ((S + TR - 1) / TR - 1) * TR);
+      }
       dtf = (float)bd.dt;
       csf = (float)(R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx));
     }
     const ResOffsets of = res_offsets(d);
-    const int LD = d.LD, LDI = d.LDI, LDY = d.LDY, rows = d.rows, nf = d.nf;
+    const int LD = d.LD, LDI = d.LDI, LDY = d.LDY, rows = d.rows;
     float* vA = fsm + obase + of.vA;
     float* vB = fsm + obase + of.vB;
     const float* miS = fsm + obase + of.mi;
@@ -597,6 +653,7 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
     const int cstrV = rows * LD, cstrI = d.S * LDI;
     const int j0 = R + jj0;
     const bool col2 = jj0 + 1 < Ni;   // odd Ni: the tile's second column is ring
+    const bool run = yshfl ? q >= 0 : active;   // lanes that run the stencil (whole warps if yshfl)
     const float2 cs2 = f2(csf, csf);
     const float2 dt2 = f2(dtf, dtf), hdt2 = f2(0.5f * dtf, 0.5f * dtf);
     const float2 half2 = f2(0.5f, 0.5f);
@@ -612,16 +669,16 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
 
       for (int n = 0; n < a.msteps; ++n) {
         const float om = a.om32[n + 1];
-        if (active) {
+        if (run) {
           // Stage 1: k1 = f(m_init + v, H(m_init) + H(v)); vB = v + dt k1.
           float2 Hs[3][TR];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            tile_stencil<R, TR>(vA + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
+            tile_stencil<R, TR>(vA + c * cstrV, LD, ii0 + R, j0, afx, LDI, jj0, afy, LDY, ii0, yshfl, Hs[c]);
 #pragma unroll
           for (int t = 0; t < TR; ++t) {
             const int ii = ii0 + t;
-            if (ii >= S) continue;
+            if (!active || ii >= S) continue;
             const int ro = ii * LDI + jj0;
             const int vo = (ii + R) * LD + j0 + 1;
             float2 v[3], m[3], H[3], f[3];
@@ -648,16 +705,16 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
           cg::this_cluster().sync();
         }
         float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
-        if (active) {
+        if (run) {
           // Stage 2: k2 = f(m_init + vB); v += dt/2 (k1 + k2) + projection, compensated.
           float2 Hs[3][TR];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            tile_stencil<R, TR>(vB + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
+            tile_stencil<R, TR>(vB + c * cstrV, LD, ii0 + R, j0, afx, LDI, jj0, afy, LDY, ii0, yshfl, Hs[c]);
 #pragma unroll
           for (int t = 0; t < TR; ++t) {
             const int ii = ii0 + t;
-            if (ii >= S) continue;
+            if (!active || ii >= S) continue;
             const int ro = ii * LDI + jj0;
             const int vo = (ii + R) * LD + j0 + 1;
             float2 mi[3], m[3], H[3], k2[3], vh[3], dd[3], vt[3], vbo[3];
@@ -736,15 +793,15 @@ micro_fp32_2d_kernel(MicroArgs a, ResLaunch L) {
           const float* in = st == 0 ? vA : (st == 2 ? vC : vB);   // this stage's state
           float* out = st == 1 ? vC : vB;                         // the next stage's state (st < 3)
           const float2 cnext = st == 2 ? dt2 : hdt2;              // its coefficient of k
-          if (active) {
+          if (run) {
             float2 Hs[3][TR];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-              tile_stencil<R, TR>(in + c * cstrV, LD, rows, ii0 + R, j0, afx, LDI, nf, jj0, afy, LDY, ii0, S, Hs[c]);
+              tile_stencil<R, TR>(in + c * cstrV, LD, ii0 + R, j0, afx, LDI, jj0, afy, LDY, ii0, yshfl, Hs[c]);
 #pragma unroll
             for (int t = 0; t < TR; ++t) {
               const int ii = ii0 + t;
-              if (ii >= S) continue;
+              if (!active || ii >= S) continue;
               const int ro = ii * LDI + jj0;
               const int vo = (ii + R) * LD + j0 + 1;
               float2 mi[3], v[3], m[3], H[3], k[3];

@@ -253,6 +253,29 @@ def test_uneven_boxes_parity(torch_cuda, precision):
 
 RESIDENT_2D = ["2d_small", "2d_ragged", "2d_order2", "2d_slow_fast"]
 
+# Row groups of 16 or 32 tiles with two lanes of slack take the right-hand y faces
+# from the next lanes by shuffles: odd interior widths (the tile's second column is
+# ring), both stencil orders, the two-lane slack exactly (Ni = 28 and 60 on the box-
+# stride instance, when the plan picks it), a cluster of CTAs and RK4P.
+YSHFL = {
+    "canvas64_odd_n63": ("c2_2d", dict(n_macro=(5, 6, 1), box_n=63, micro_steps=30)),
+    "order2_odd_n27": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=27, micro_steps=40, stencil_order=2)),
+    "slack2_n34": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=34, micro_steps=30)),
+    "slack2_n66": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=66, micro_steps=24)),
+    "rk4p_n63": ("c2_2d", dict(n_macro=(5, 5, 1), box_n=63, micro_steps=24, micro_stepper=1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(YSHFL))
+def test_resident_2d_shuffled_y_faces(torch_cuda, case):
+    name, over = YSHFL[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, _ = gpu_micro(torch_cuda, cfg, M0, 1, kernel_variant=2)
+    pts = sorted(set([0, 1, cfg.n_points // 2, cfg.n_points - 1]))
+    Hr = O.micro_batch(cfg, M0, points=pts)
+    assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
+
 
 @pytest.mark.parametrize("case", RESIDENT_2D)
 def test_resident_2d_kernel_parity(torch_cuda, case):
