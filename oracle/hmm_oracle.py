@@ -19,8 +19,8 @@ methods for the Landau-Lifshitz equation", step by step and in FP64:
 * the micro problem (Section 2.2, eq. micro) on [-mu', mu']^d with Dirichlet
   conditions on m - m_init (Section 4.2), H = div(a^eps grad m) by a
   conservative staggered difference (2nd order as in Section 2.3, or 4th order);
-* HeunP time stepping (Section 3.1) with the micro time step bounded by the
-  stability condition eq. Cstab (Section 3.2);
+* HeunP, RK4P, MPE or MPEA micro time stepping (Section 3.1) with the micro
+  time step bounded by the stability condition eq. Cstab (Section 3.2);
 * the field-model macro step (Section 2.2, eq. macro_disc) by MPEA
   (Section 3.1, eqs. h_term, h_mpea, mpe_update) or MPE (eq. h_mpe) with an
   RK4P start-up.
@@ -158,27 +158,44 @@ def time_weights(M: int, p: int, q: int, dtype=np.float64) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 
-def _amplification(stepper: int):
-    """Stability polynomial of the stepper: HeunP (0) 1 + z + z^2/2, RK4P (1) its
-    continuation to z^4/24 (Section 3.2, the related Runge-Kutta methods)."""
-    if stepper == 0:
-        return lambda z: 1.0 + z + 0.5 * z * z
-    if stepper == 1:
-        return lambda z: 1.0 + z * (1.0 + z * (0.5 + z * (1.0 / 6.0 + z / 24.0)))
-    raise ValueError("micro_stepper must be 0 (HeunP) or 1 (RK4P)")
+HEUNP, RK4P, MICRO_MPE, MICRO_MPEA = 0, 1, 2, 3   # micro steppers (Section 3.1)
+
+
+def _growth(stepper: int):
+    """Growth factor of the stepper's linear stability analysis at z = lambda dt.
+
+    HeunP (0) and RK4P (1): |R(z)| with R = 1 + z + z^2/2 and its continuation to
+    z^4/24 (the related Runge-Kutta methods, Section 3.2). MPE (2) and MPEA (3): the
+    largest root modulus of the characteristic polynomial of the related
+    Adams-Bashforth method, AB2 and AB3 (Section 3.2 relates MPE and MPEA to AB2 and
+    AB3 and finds their stability limits almost equal): rho(zeta) - z sigma(zeta) with
+    rho = zeta^2 - zeta, sigma = (3 zeta - 1)/2 (AB2) and rho = zeta^3 - zeta^2,
+    sigma = (23 zeta^2 - 16 zeta + 5)/12 (AB3). A reading: the paper plots the
+    stability limits but prints no rule, and the library takes the related method's.
+    """
+    if stepper == HEUNP:
+        return lambda z: abs(1.0 + z + 0.5 * z * z)
+    if stepper == RK4P:
+        return lambda z: abs(1.0 + z * (1.0 + z * (0.5 + z * (1.0 / 6.0 + z / 24.0))))
+    if stepper == MICRO_MPE:
+        return lambda z: max(abs(r) for r in np.roots([1.0, -1.0 - 1.5 * z, 0.5 * z]))
+    if stepper == MICRO_MPEA:
+        return lambda z: max(abs(r) for r in np.roots([1.0, -1.0 - 23.0 / 12.0 * z, 16.0 / 12.0 * z,
+                                                       -5.0 / 12.0 * z]))
+    raise ValueError("micro_stepper must be 0 (HeunP), 1 (RK4P), 2 (MPE) or 3 (MPEA)")
 
 
 def stability_limit(alpha: float, stepper: int = 0) -> float:
-    """Largest s > 0 with |R(z)| <= 1 for z = s(-alpha + i), R the stepper's polynomial.
+    """Largest s > 0 with growth <= 1 for z = s(-alpha + i) (``_growth``).
 
     The linearised LL Jacobian has eigenvalues (+-i - alpha) omega (Section 3.2).
     Scans outward from s = 0 and bisects the first exit from the unit disc.
     """
     w = complex(-alpha, 1.0)
-    R = _amplification(stepper)
+    g = _growth(stepper)
 
     def amp(s):
-        return abs(R(s * w))
+        return g(s * w)
 
     s, ds = 0.0, 1e-3
     while amp(s + ds) <= 1.0:
@@ -214,7 +231,8 @@ def coef_upper_bound(cfg) -> float:
 
 def micro_dt(cfg, dx: float, a_max: Optional[float] = None) -> float:
     """Micro time step dt = safety * s_max(alpha_micro) / omega_max (a reading: the
-    paper states only dt <= C_stab dx^2, eq. Cstab), s_max the stability limit of the micro stepper (HeunP or RK4P).
+    paper states only dt <= C_stab dx^2, eq. Cstab), s_max the stability limit of the
+    micro stepper (``stability_limit``).
 
     omega_max = a_max * d * lambda_s / dx^2 bounds the spectral radius of
     -div(a grad) for the staggered stencil; a_max = c0 + sum |amp|.
@@ -477,6 +495,33 @@ def _interior(arr: np.ndarray, d: int, r: int) -> Tuple:
     return (Ellipsis,) + tuple(slice(r, arr.shape[-d + k] - r) for k in range(d))
 
 
+def midpoint_solve(m: np.ndarray, h: np.ndarray, dt: float, axis: int) -> np.ndarray:
+    """m' with (m' - m)/dt = -(m + m')/2 x h at every node (eq. mpe_update).
+
+    As in ``midpoint_update``: with w = dt/2 h and [w]_x v = w x v, (I - [w]_x) m' =
+    (I + [w]_x) m, one 3x3 system per node (components along ``axis``), solved by
+    Cramer's rule (plain arithmetic, so any working precision).
+    """
+    mm = np.moveaxis(m, axis, -1)
+    w = 0.5 * dt * np.moveaxis(h, axis, -1)
+    z = np.zeros_like(w[..., 0])
+    one = z + 1
+    wx = [[z, -w[..., 2], w[..., 1]],
+          [w[..., 2], z, -w[..., 0]],
+          [-w[..., 1], w[..., 0], z]]                       # wx @ v = w x v
+    A = [[(one if i == j else z) - wx[i][j] for j in range(3)] for i in range(3)]
+    b = [mm[..., i] + sum(wx[i][j] * mm[..., j] for j in range(3)) for i in range(3)]
+
+    def det(c0, c1, c2):   # determinant of the matrix with columns c0, c1, c2
+        return (c0[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - c1[0] * (c0[1] * c2[2] - c0[2] * c2[1])
+                + c2[0] * (c0[1] * c1[2] - c0[2] * c1[1]))
+
+    cols = [[A[i][j] for i in range(3)] for j in range(3)]
+    dA = det(*cols)
+    out = [det(*[b if j == k else cols[j] for j in range(3)]) / dA for k in range(3)]
+    return np.moveaxis(np.stack(out, -1), -1, axis)
+
+
 def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: float,
                 M: int, alpha_micro: float, W: np.ndarray, w: np.ndarray, order: int,
                 trace: bool = False, stepper: int = 0, flux: Optional[Tuple[int, np.ndarray]] = None):
@@ -489,7 +534,12 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
     (Section 3.1): k1 = f(m^n), k2 = f(m^n + dt/2 k1), k3 = f(m^n + dt/2 k2),
     k4 = f(m^n + dt k3), m~ = m^n + dt/6 (k1 + 2 k2 + 2 k3 + k4), m^{n+1} =
     m~/|m~| (the third stage read as above, where the printed stage repeats
-    k_2). Only interior nodes move;
+    k_2); with stepper = 2 (MPE) or 3 (MPEA) by the midpoint update with an
+    extrapolated h (Section 3.1, eqs. h_term, h_mpe, h_mpea, mpe_update), node by
+    node: h^n = H(m^n) + alpha m^n x H(m^n), h^{n+1/2} by ``extrapolate_h`` and
+    m^{n+1} from (m^{n+1} - m^n)/dt = -(m^n + m^{n+1})/2 x h^{n+1/2}, after
+    start-up steps by RK4P (one for MPE, two for MPEA; a reading: the paper allows
+    HeunP or RK4P, and RK4P is what the macro stepper uses). Only interior nodes move;
     ring nodes keep m_init (Dirichlet on m - m_init, Section 4.2).
     The average (eq. upscaling) is sum_n w_n sum_xi W(xi) H(m^n)(xi), with
     H(m^n) the stage-1 field of step n (a reading: the paper does not say which
@@ -510,6 +560,7 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
     Wb = W[(None,) * (cax + 1)] if W is not None else None
     red = tuple(range(cax + 1, m.ndim))
     energies, normdev = [], []
+    hist: List[np.ndarray] = []   # [h^{n-1}, h^{n-2}] (MPE, MPEA)
     if flux is not None:
         fk, Wf = flux
         fax = cax + 1 + fk
@@ -540,6 +591,14 @@ def micro_solve(m_init: np.ndarray, afaces: List[np.ndarray], dx: float, dt: flo
             ms[inner] = mi + c * k
             return ll_rhs(ms[inner], field_H(ms, afaces, dx, order), alpha_micro, axis=cax)
 
+        if stepper >= MICRO_MPE:
+            hn = H1 + alpha_micro * np.cross(mi, H1, axis=cax)   # eq. h_term at m^n
+            if n >= (1 if stepper == MICRO_MPE else 2):
+                hx = extrapolate_h(hn, hist, MPE if stepper == MICRO_MPE else MPEA)
+                m[inner] = midpoint_solve(mi, hx, dt, cax)
+                hist = [hn] + hist[:1]
+                continue
+            hist = [hn] + hist[:1]
         if stepper == 0:
             k2 = stage(dt, k1)
             mt = mi + 0.5 * dt * (k1 + k2)
