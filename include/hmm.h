@@ -53,10 +53,16 @@ typedef enum {
 /* Time integrator of the micro problems (Section 3.1): HeunP, the paper's choice
  * with artificial damping (Section 3.4), or RK4P, whose stability region holds
  * part of the imaginary axis and which is cheaper per unit of micro time for
- * small micro damping (Section 3.2). */
+ * small micro damping (Section 3.2); or the multi-step midpoint methods MPE and
+ * MPEA (eqs. h_mpe, h_mpea, mpe_update: one stencil evaluation per step, after one
+ * (MPE) or two (MPEA) RK4P start-up steps), whose time step follows the stability
+ * regions of AB2 and AB3 (Section 3.2, eq. mpe_update_ab). MPE and MPEA run on the
+ * generic kernels (both precisions). */
 typedef enum {
   HMM_HEUNP = 0,
-  HMM_RK4P = 1
+  HMM_RK4P = 1,
+  HMM_MICRO_MPE = 2,
+  HMM_MICRO_MPEA = 3
 } hmm_micro_stepper;
 
 /* Macro time stepper (Section 3.1): MPEA, the extrapolation of eq. h_mpea in the
@@ -132,7 +138,8 @@ typedef struct {
                                    2 resident                                      */
   int micro_stepper;            /* hmm_micro_stepper; with RK4P the automatic kernel
                                    choice takes the resident kernel in 2D and the
-                                   generic kernel in 3D                            */
+                                   generic kernel in 3D; MPE and MPEA take the
+                                   generic kernel                                  */
   int model;                    /* hmm_model                                       */
   int macro_stepper;            /* hmm_macro_stepper (0: MPEA, 1: MPE)             */
   int tile_rows;                /* resident 2D kernel, rows per thread tile: 0 the

@@ -221,11 +221,67 @@ double rk4_limit(double a) {
   return lo;
 }
 
+// Largest root modulus of the characteristic polynomial rho(zeta) - z sigma(zeta) of
+// AB2 (k = 2) or AB3 (k = 3), the methods Section 3.2 relates MPE and MPEA to
+// (eq. mpe_update_ab): zeta^2 - (1 + 3z/2) zeta + z/2 and
+// zeta^3 - (1 + 23z/12) zeta^2 + (16z/12) zeta - 5z/12; roots by Durand-Kerner.
+double ab_growth(std::complex<double> z, int k) {
+  using C = std::complex<double>;
+  C c[4];   // monic, c[0] zeta^k + c[1] zeta^(k-1) + ...
+  if (k == 2) {
+    c[0] = 1.0; c[1] = -(1.0 + 1.5 * z); c[2] = 0.5 * z;
+  } else {
+    c[0] = 1.0; c[1] = -(1.0 + (23.0 / 12.0) * z); c[2] = (16.0 / 12.0) * z; c[3] = -(5.0 / 12.0) * z;
+  }
+  auto P = [&](C x) {
+    C v = c[0];
+    for (int i = 1; i <= k; ++i) v = v * x + c[i];
+    return v;
+  };
+  C r[3];
+  for (int i = 0; i < k; ++i) r[i] = std::pow(C(0.4, 0.9), i);
+  for (int it = 0; it < 500; ++it) {
+    for (int i = 0; i < k; ++i) {
+      C den = 1.0;
+      for (int j = 0; j < k; ++j)
+        if (j != i) den *= r[i] - r[j];
+      r[i] -= P(r[i]) / den;
+    }
+  }
+  double g = 0.0;
+  for (int i = 0; i < k; ++i) g = std::max(g, std::abs(r[i]));
+  return g;
+}
+
+double ab_limit(double a, int k) {
+  const std::complex<double> ray(-a, 1.0);
+  double lo = 0.0, hi = 1e-3;
+  while (ab_growth(hi * ray, k) <= 1.0) {
+    lo = hi;
+    hi += 1e-3;
+    if (hi > 20.0) return 0.0;
+  }
+  for (int it = 0; it < 100; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (ab_growth(mid * ray, k) <= 1.0) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+double stepper_limit(double alpha_micro, int stepper) {
+  switch (stepper) {
+    case HMM_RK4P: return rk4_limit(alpha_micro);
+    case HMM_MICRO_MPE: return ab_limit(alpha_micro, 2);
+    case HMM_MICRO_MPEA: return ab_limit(alpha_micro, 3);
+    default: return heun_limit(alpha_micro);
+  }
+}
+
 double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order, double dx,
                 int stepper) {
   const double lam = stencil_order == 2 ? 4.0 : (28.0 / 12.0) * (28.0 / 12.0);
   const double omega = a_max * dim * lam / (dx * dx);
-  return dt_safety * (stepper == 1 ? rk4_limit(alpha_micro) : heun_limit(alpha_micro)) / omega;
+  return dt_safety * stepper_limit(alpha_micro, stepper) / omega;
 }
 
 }  // namespace host
@@ -491,8 +547,8 @@ hmm_status build(HmmHandle* h) {
   if (p.model != HMM_FIELD_MODEL && p.model != HMM_FLUX_MODEL)
     return fail(h, HMM_ERR_INVALID_ARG, "model must be 0 (field) or 1 (flux)");
 
-  if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
-    return fail(h, HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
+  if (p.micro_stepper < HMM_HEUNP || p.micro_stepper > HMM_MICRO_MPEA)
+    return fail(h, HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP), 1 (RK4P), 2 (MPE) or 3 (MPEA)");
   h->dim = p.dim;
   if (!(p.L > 0)) p.L = 1.0;
   if (p.px <= 0) p.px = 3;
@@ -697,7 +753,7 @@ hmm_status build(HmmHandle* h) {
   int optin = 0;
   HMM_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
   std::string why = "the resident kernels need the FP32 form and d = 2 (HeunP or RK4P) or d = 3 (HeunP)";
-  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 &&
+  const bool res_ok = p.precision == HMM_FP32_BATCHED && h->dim >= 2 && p.micro_stepper <= HMM_RK4P &&
                       (p.micro_stepper == HMM_HEUNP || h->dim == 2) &&
                       res2d_make_plan(h->dim, h->boxes.data(), h->nb, h->radius, h->interp_k, p.n_terms,
                                       (size_t)optin - 256, &h->plan, &why, nullptr, true, p.micro_stepper,
@@ -721,8 +777,8 @@ hmm_status build(HmmHandle* h) {
     HMM_CUDA(h, p.precision == HMM_FP64_PLAIN
                     ? prepare_micro_fp64(h->dim, h->radius, h->block, h->smem, &per_sm)
                     : prepare_micro_fp32(h->dim, h->radius, h->block, h->smem, &per_sm));
-    h->slot_bytes = p.precision == HMM_FP64_PLAIN ? micro_slot_bytes_fp64(h->dim, h->nmax)
-                                                  : micro_slot_bytes_fp32(h->dim, h->nmax);
+    h->slot_bytes = p.precision == HMM_FP64_PLAIN ? micro_slot_bytes_fp64(h->dim, h->nmax, p.micro_stepper)
+                                                  : micro_slot_bytes_fp32(h->dim, h->nmax, p.micro_stepper);
   }
   if (per_sm < 1) return fail(h, HMM_ERR_INVALID_ARG, "micro kernel does not fit on an SM for this box size");
   h->grid = h->res2d ? res2d_max_grid(h->plan) : std::min(h->nb, per_sm * h->num_sms);
@@ -972,8 +1028,8 @@ hmm_status hmm_micro_batch_points(void* handle, const double* M_dev, double* Hav
   HMM_CUDA(h, h->p.precision == HMM_FP64_PLAIN ? prepare_micro_fp64(h->dim, h->radius, block, smem, &per_sm)
                                                 : prepare_micro_fp32(h->dim, h->radius, block, smem, &per_sm));
   if (per_sm < 1) return fail(h, HMM_ERR_INVALID_ARG, "micro kernel does not fit on an SM for this box size");
-  const size_t slot = h->p.precision == HMM_FP64_PLAIN ? micro_slot_bytes_fp64(h->dim, nmax)
-                                                        : micro_slot_bytes_fp32(h->dim, nmax);
+  const size_t slot = h->p.precision == HMM_FP64_PLAIN ? micro_slot_bytes_fp64(h->dim, nmax, h->p.micro_stepper)
+                                                        : micro_slot_bytes_fp32(h->dim, nmax, h->p.micro_stepper);
   const int grid = std::min(n_points, per_sm * h->num_sms);
   HMM_TRY(begin_call(h));
   if (n_points > h->sub_cap) {

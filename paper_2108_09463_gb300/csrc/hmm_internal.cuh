@@ -80,8 +80,8 @@ cudaError_t launch_micro_fp64(const MicroArgs& a, int dim, int radius, int grid,
 cudaError_t launch_micro_fp32(const MicroArgs& a, int dim, int radius, int grid, int block,
                               size_t smem, cudaStream_t st);
 // Per-CTA arena bytes for boxes of up to nmax nodes per axis.
-size_t micro_slot_bytes_fp64(int dim, int nmax);
-size_t micro_slot_bytes_fp32(int dim, int nmax);
+size_t micro_slot_bytes_fp64(int dim, int nmax, int stepper);   // stepper >= 2: MPE(A) history
+size_t micro_slot_bytes_fp32(int dim, int nmax, int stepper);
 // Dynamic shared memory of the set-up tables.
 size_t micro_smem_bytes(int dim, int nmax, int interp_k, int n_terms);
 // Set the kernel's dynamic shared-memory limit and return resident CTAs per SM.
@@ -160,6 +160,9 @@ double eval_kernel0(const double* c, int p, int q, double t);
 double heun_limit(double alpha);
 // Largest s with |1 + z + z^2/2 + z^3/6 + z^4/24| <= 1 on z = s(-alpha + i) (RK4P).
 double rk4_limit(double alpha);
+// Largest s with every root of AB2's (k = 2) or AB3's (k = 3) characteristic polynomial
+// in the unit disc on z = s(-alpha + i) (MPE, MPEA).
+double ab_limit(double alpha, int k);
 double micro_dt(double dt_safety, double alpha_micro, double a_max, int dim, int stencil_order, double dx,
                 int stepper);
 }  // namespace host

@@ -15,6 +15,9 @@
 //    on the ring, (sum_n w_n) sum_xi W H(m_init) + sum_xi H(W)(xi) V(xi) with
 //    V = sum_n w_n v^n. V is accumulated per node in FP32 with Kahan
 //    compensation; H(W) and both contractions are evaluated in FP64.
+//  * MPE and MPEA (Section 3.1) keep h^n = H + alpha m x H per node for the next
+//    steps and take the midpoint update in closed form (the Cayley transform, as
+//    in the FP64 kernel); its increment goes through the same compensated sum.
 //  * The HeunP projection (Section 3.1) is applied in perturbation form: with
 //    u = m_init + v~ and s = |u|^2 - 1 (m_init taken as exactly unit, which its
 //    FP64 value is), normalise(u) - m_init = v~ + c u, c = -s/(sqrt(1+s)(1+sqrt(1+s))),
@@ -37,13 +40,15 @@ struct Fp32Slot {
   float* V;      // [3][cap] sum_n w_n v_hi^n
   float* Vc;     // [3][cap] Kahan compensation of V
   float* vC;     // [3][cap] second stage state (RK4P)
+  float* hX;     // [3][cap] MPE(A): h^{n-1} (only in slots sized for them)
+  float* hY;     // [3][cap] MPE(A): h^{n-2}, overwritten by h^n
 };
 
 __host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-__host__ __device__ inline size_t fp32_slot_bytes(int D, size_t cap) {
+__host__ __device__ inline size_t fp32_slot_bytes(int D, size_t cap, int stepper) {
   return align256(3 * cap * 8) + align256(D * cap * 8) + 2 * align256(3 * cap * 4) +
-         align256(D * cap * 4) + 7 * align256(3 * cap * 4);
+         align256(D * cap * 4) + (stepper >= 2 ? 9 : 7) * align256(3 * cap * 4);
 }
 
 __device__ inline Fp32Slot carve_fp32(char* base, int D, size_t cap) {
@@ -62,6 +67,8 @@ __device__ inline Fp32Slot carve_fp32(char* base, int D, size_t cap) {
   s.V = reinterpret_cast<float*>(take(3 * cap * 4));
   s.Vc = reinterpret_cast<float*>(take(3 * cap * 4));
   s.vC = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.hX = reinterpret_cast<float*>(take(3 * cap * 4));
+  s.hY = reinterpret_cast<float*>(take(3 * cap * 4));
   return s;
 }
 
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
   const SetupSmem sm = carve_setup(smem, D, nmax, a.interp_k, a.n_terms);
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t cap = (size_t)ipow<D>(nmax);
-  const Fp32Slot sl = carve_fp32(a.arena + (size_t)blockIdx.x * a.slot_bytes, D, cap);
+  Fp32Slot sl = carve_fp32(a.arena + (size_t)blockIdx.x * a.slot_bytes, D, cap);
   const float am = (float)a.alpha_micro;
 
   for (;;) {
@@ -204,12 +211,17 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
     __syncthreads();
 
     const float dt = (float)bd.dt, hdt = 0.5f * (float)bd.dt;
-    const bool rk4 = a.stepper == 1;
-    // HeunP: v_B = v + dt k1, d = dt/2 (k1 + k2). RK4P: v_B = v + dt/2 k1, the sum
-    // k1 + 2 k2 + 2 k3 accumulated in sl.k1, d = dt/6 (k1 + 2 k2 + 2 k3 + k4).
-    const float cb1 = rk4 ? hdt : dt, cdl = rk4 ? (float)(bd.dt / 6.0) : hdt;
+    const bool mpe = a.stepper >= 2;                 // MPE (2) or MPEA (3)
+    const int nstart = a.stepper == 2 ? 1 : 2;       // their RK4P start-up steps
+    const float e0 = a.stepper == 2 ? 1.5f : (float)(23.0 / 12.0), e1 = a.stepper == 2 ? -0.5f : (float)(-16.0 / 12.0),
+                e2 = a.stepper == 2 ? 0.f : (float)(5.0 / 12.0);
     for (int n = 0; n < a.msteps; ++n) {
       const float wn = a.w32[n];
+      const bool mp = mpe && n >= nstart;            // a midpoint step of MPE(A)
+      const bool rk4 = a.stepper == 1 || (mpe && !mp);
+      // HeunP: v_B = v + dt k1, d = dt/2 (k1 + k2). RK4P: v_B = v + dt/2 k1, the sum
+      // k1 + 2 k2 + 2 k3 accumulated in sl.k1, d = dt/6 (k1 + 2 k2 + 2 k3 + k4).
+      const float cb1 = rk4 ? hdt : dt, cdl = rk4 ? (float)(bd.dt / 6.0) : hdt;
       // Stage 1: k1 = f(m_init + v), v_B = v + dt k1, V += w_n v (Kahan).
       for (int t = tid; t < nint; t += nt) {
         const int idx = interior_node<D, R>(t, N);
@@ -223,19 +235,61 @@ __global__ void __launch_bounds__(256) micro_fp32_kernel(MicroArgs a) {
           v[c] = sl.vA[c * cap + idx];
           m[c] = sl.mi32[c * cap + idx] + v[c];
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {   // V += w_n v^n (Kahan)
+          const size_t o = c * cap + idx;
+          const float y = wn * v[c] - sl.Vc[o];
+          const float tV = sl.V[o] + y;
+          sl.Vc[o] = (tV - sl.V[o]) - y;
+          sl.V[o] = tV;
+        }
+        if (mpe) {
+          // h^n (eq. h_term), kept as h^{n-1} for the next step (in hY, whose h^{n-2}
+          // this step reads first)
+          const float hn[3] = {Hv[0] + am * (m[1] * Hv[2] - m[2] * Hv[1]), Hv[1] + am * (m[2] * Hv[0] - m[0] * Hv[2]),
+                               Hv[2] + am * (m[0] * Hv[1] - m[1] * Hv[0])};
+          if (mp) {
+            float w[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              w[c] = hdt * (e0 * hn[c] + e1 * sl.hX[c * cap + idx] + e2 * sl.hY[c * cap + idx]);
+            const float wm[3] = {w[1] * m[2] - w[2] * m[1], w[2] * m[0] - w[0] * m[2], w[0] * m[1] - w[1] * m[0]};
+            const float g = 2.f / (1.f + (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+            const float d[3] = {g * (wm[0] + (w[1] * wm[2] - w[2] * wm[1])), g * (wm[1] + (w[2] * wm[0] - w[0] * wm[2])),
+                                g * (wm[2] + (w[0] * wm[1] - w[1] * wm[0]))};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {   // v^{n+1} = v^n + d, compensated, into vB
+              const size_t o = c * cap + idx;
+              const float inc = d[c] + sl.vlo[o];
+              const float nh = v[c] + inc;
+              sl.vlo[o] = inc - (nh - v[c]);
+              sl.vB[o] = nh;
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) sl.hY[c * cap + idx] = hn[c];
+          if (mp) continue;
+        }
         ll_rhs(m, Hv, am, k1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const size_t o = c * cap + idx;
           sl.k1[o] = k1[c];
           sl.vB[o] = v[c] + cb1 * k1[c];
-          const float y = wn * v[c] - sl.Vc[o];
-          const float tV = sl.V[o] + y;
-          sl.Vc[o] = (tV - sl.V[o]) - y;
-          sl.V[o] = tV;
         }
       }
       __syncthreads();
+      if (mpe) {   // h^n becomes h^{n-1}, h^{n-1} becomes h^{n-2}
+        float* t = sl.hX;
+        sl.hX = sl.hY;
+        sl.hY = t;
+      }
+      if (mp) {    // v^{n+1} was written to vB
+        float* t = sl.vA;
+        sl.vA = sl.vB;
+        sl.vB = t;
+        continue;
+      }
       if (rk4) {
         // RK4P stages 2 and 3: k2 = f(m_init + v + dt/2 k1) (state in v_B), k3 =
         // f(m_init + v + dt/2 k2) (state in v_C); the last stage's state v + dt k3 goes to v_B.
@@ -388,10 +442,10 @@ cudaError_t prepare_micro_fp32(int dim, int radius, int block, size_t smem, int*
   HMM_DISPATCH(prepare_t, block, smem, ctas_per_sm);
 }
 
-size_t micro_slot_bytes_fp32(int dim, int nmax) {
+size_t micro_slot_bytes_fp32(int dim, int nmax, int stepper) {
   size_t cap = 1;
   for (int i = 0; i < dim; ++i) cap *= (size_t)nmax;
-  return align256(fp32_slot_bytes(dim, cap));
+  return align256(fp32_slot_bytes(dim, cap, stepper));
 }
 
 }  // namespace hmm

@@ -1,5 +1,5 @@
 // Plain FP64 micro-batch kernel: the micro problem (eq. micro) of every macro
-// point, stepped by HeunP or RK4P (Section 3.1) with the Dirichlet ring (Section 4.2),
+// point, stepped by HeunP, RK4P, MPE or MPEA (Section 3.1) with the Dirichlet ring (Section 4.2),
 // and reduced by the kernel-weighted average (Section 2.3, eq. upscaling), all
 // in FP64 arithmetic. One CTA per box, boxes pulled from an atomic queue.
 //
@@ -9,6 +9,13 @@
 // FP64 rounding floor of H_avg drops from ~1e-12 (the m-form) to ~1e-15.
 // The projection m^{n+1} = m~/|m~| becomes v^{n+1} = v~ + c (m_init + v~) with
 // s = |m_init + v~|^2 - 1 and c = -s / (sqrt(1+s) (1 + sqrt(1+s))).
+//
+// MPE and MPEA (eqs. h_mpe, h_mpea, mpe_update): after one (MPE) or two (MPEA)
+// RK4P start-up steps, h^n = H(m^n) + alpha m^n x H(m^n) (eq. h_term) is kept per
+// node for the next steps, h^{n+1/2} extrapolated from h^n, h^{n-1} (and h^{n-2}),
+// and the midpoint update solved per node in closed form: with w = dt/2 h^{n+1/2},
+// (I - [w]x) m' = (I + [w]x) m gives m' = m + 2/(1 + |w|^2) (w x m + w x (w x m))
+// (the Cayley transform; (I - [w]x)^{-1} = I + ([w]x + [w]x^2)/(1 + |w|^2)).
 #include "micro_common.cuh"
 #include "stencil.cuh"
 
@@ -26,9 +33,11 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
   double* hi = mi + 3 * cap;  // H(m_init)
   double* vA = hi + 3 * cap;
   double* vB = vA + 3 * cap;
-  double* q = vB + 3 * cap;   // the step's accumulated state v + dt sum b_i k_i
+  double* q = vB + 3 * cap;   // the step's accumulated state v + dt sum b_i k_i (MPE(A): v^{n+1})
   double* vC = q + 3 * cap;   // second stage state (RK4P)
   double* af = vC + 3 * cap;
+  double* hX = af + D * cap;  // MPE(A): h^{n-1} (only in slots sized for them)
+  double* hY = hX + 3 * cap;  // MPE(A): h^{n-2}, overwritten by h^n
 
   for (;;) {
     const int b = next_box(a.queue, &s_box);
@@ -68,9 +77,10 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
     __syncthreads();
 
     const double dt = bd.dt, hdt = 0.5 * bd.dt;
-    const bool rk4 = a.stepper == 1;
-    // stage-1 coefficients: q = v + cq1 k1, vB = v + cb1 k1; the last stage adds cql k_last
-    const double cq1 = rk4 ? dt / 6.0 : hdt, cb1 = rk4 ? hdt : dt, cql = rk4 ? dt / 6.0 : hdt;
+    const bool mpe = a.stepper >= 2;                 // MPE (2) or MPEA (3)
+    const int nstart = a.stepper == 2 ? 1 : 2;       // their RK4P start-up steps
+    const double e0 = a.stepper == 2 ? 1.5 : 23.0 / 12.0, e1 = a.stepper == 2 ? -0.5 : -16.0 / 12.0,
+                 e2 = a.stepper == 2 ? 0.0 : 5.0 / 12.0;
     const double cs = R == 3 ? 1.0 / ((24.0 * bd.dx) * (24.0 * bd.dx)) : 1.0 / (bd.dx * bd.dx);
     const double* W1 = a.W64 + bd.wofs;
     const int nint = ipow<D>(N - 2 * R);
@@ -129,6 +139,10 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
     for (int n = 0; n <= a.msteps; ++n) {
       const double wn = a.w64[n];
       if (n == a.msteps && wn == 0.0) break;  // K0(1) = 0: no final stencil pass
+      const bool mp = mpe && n >= nstart;      // a midpoint step of MPE(A)
+      const bool rk4 = a.stepper == 1 || (mpe && !mp);
+      // stage-1 coefficients: q = v + cq1 k1, vB = v + cb1 k1; the last stage adds cql k_last
+      const double cq1 = rk4 ? dt / 6.0 : hdt, cb1 = rk4 ? hdt : dt, cql = rk4 ? dt / 6.0 : hdt;
       if (fax >= 0 && wn != 0.0) flux_sum(vA, wn, acc0, acc1, acc2);   // v^n is read-only in stage 1
       if (fax >= 0 && n == a.msteps) break;
       // Stage 1: H(m^n) = H(m_init) + H(v^n), its weighted sum, k1, v + dt k1, v + dt/2 k1.
@@ -155,6 +169,30 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
           m[c] = mi[c * cap + idx] + v[c];
           H[c] = hi[c * cap + idx] + Hv[c];
         }
+        if (mpe) {
+          // h^n (eq. h_term), kept as h^{n-1} for the next step (in hY, whose h^{n-2}
+          // this step reads first)
+          const double h0 = H[0] + a.alpha_micro * (m[1] * H[2] - m[2] * H[1]);
+          const double h1 = H[1] + a.alpha_micro * (m[2] * H[0] - m[0] * H[2]);
+          const double h2 = H[2] + a.alpha_micro * (m[0] * H[1] - m[1] * H[0]);
+          if (mp) {
+            double w[3];
+            const double hn[3] = {h0, h1, h2};
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              w[c] = hdt * (e0 * hn[c] + e1 * hX[c * cap + idx] + e2 * hY[c * cap + idx]);
+            const double wm0 = w[1] * m[2] - w[2] * m[1], wm1 = w[2] * m[0] - w[0] * m[2],
+                         wm2 = w[0] * m[1] - w[1] * m[0];
+            const double g = 2.0 / (1.0 + (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+            q[idx] = v[0] + g * (wm0 + (w[1] * wm2 - w[2] * wm1));
+            q[cap + idx] = v[1] + g * (wm1 + (w[2] * wm0 - w[0] * wm2));
+            q[2 * cap + idx] = v[2] + g * (wm2 + (w[0] * wm1 - w[1] * wm0));
+          }
+          hY[idx] = h0;
+          hY[cap + idx] = h1;
+          hY[2 * cap + idx] = h2;
+          if (mp) continue;
+        }
         ll_rhs(m, H, a.alpha_micro, k1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -164,6 +202,17 @@ __global__ void __launch_bounds__(256) micro_fp64_kernel(MicroArgs a) {
       }
       if (n == a.msteps) break;
       __syncthreads();
+      if (mpe) {   // h^n becomes h^{n-1}, h^{n-1} becomes h^{n-2}
+        double* t = hX;
+        hX = hY;
+        hY = t;
+      }
+      if (mp) {    // v^{n+1} was written to q
+        double* t = vA;
+        vA = q;
+        q = t;
+        continue;
+      }
       if (rk4) {
         // RK4P stages 2 and 3: k2 = f(v + dt/2 k1) (state in vB), k3 = f(v + dt/2 k2)
         // (state in vC); q += dt/3 (k2 + k3); the last stage's state v + dt k3 goes to vB.
@@ -280,10 +329,10 @@ size_t micro_smem_bytes(int dim, int nmax, int interp_k, int n_terms) {
   return sizeof(double) * setup_smem_doubles(dim, nmax, interp_k, n_terms);
 }
 
-size_t micro_slot_bytes_fp64(int dim, int nmax) {
+size_t micro_slot_bytes_fp64(int dim, int nmax, int stepper) {
   size_t cap = 1;
   for (int i = 0; i < dim; ++i) cap *= (size_t)nmax;
-  size_t b = (size_t)(6 * 3 + dim) * cap * sizeof(double);
+  size_t b = (size_t)(6 * 3 + dim + (stepper >= 2 ? 6 : 0)) * cap * sizeof(double);
   return (b + 255) & ~(size_t)255;
 }
 

@@ -21,7 +21,7 @@
 namespace hmm {
 
 void set_null_handle_error(const char* msg);
-size_t micro_slot_bytes_fp32(int dim, int nmax);
+size_t micro_slot_bytes_fp32(int dim, int nmax, int stepper);
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB
 constexpr int kNoAllocMaxDevices = 64;
@@ -124,8 +124,8 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
   if (p.macro_stepper != HMM_MPEA && p.macro_stepper != HMM_MPE)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "macro_stepper must be 0 (MPEA) or 1 (MPE)");
   if (p.model != HMM_FIELD_MODEL) return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free batch runs the field model");
-  if (p.micro_stepper != HMM_HEUNP && p.micro_stepper != HMM_RK4P)
-    return noalloc_fail(HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP) or 1 (RK4P)");
+  if (p.micro_stepper < HMM_HEUNP || p.micro_stepper > HMM_MICRO_MPEA)
+    return noalloc_fail(HMM_ERR_INVALID_ARG, "micro_stepper must be 0 (HeunP), 1 (RK4P), 2 (MPE) or 3 (MPEA)");
   if (p.kernel_variant != 0 && p.kernel_variant != 1)
     return noalloc_fail(HMM_ERR_INVALID_ARG, "the allocation-free entry point runs the generic kernel");
   if (!(p.L > 0)) p.L = 1.0;
@@ -193,7 +193,7 @@ extern "C" hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const do
   const size_t o_w64 = o_W32 + align256(sizeof(float) * N);
   const size_t o_w32 = o_w64 + align256(sizeof(double) * (M + 1));
   const size_t o_arena = o_w32 + align256(sizeof(float) * (M + 1));
-  const size_t slot = micro_slot_bytes_fp32(p.dim, N);
+  const size_t slot = micro_slot_bytes_fp32(p.dim, N, p.micro_stepper);
   if (o_arena + slot > kNoAllocScratchBytes) {
     std::snprintf(msg, sizeof msg,
                   "problem needs %zu bytes of scratch for one box; the allocation-free maximum is %zu",

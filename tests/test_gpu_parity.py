@@ -176,6 +176,45 @@ def test_rk4p_resident_2d(torch_cuda, case):
     assert rel_err(Hg[:, pts], Hr) < TOL[1], (case, rel_err(Hg[:, pts], Hr))
 
 
+# The multi-step micro steppers MPE (2) and MPEA (3) on the generic kernels, both
+# precisions: RK4P start-up steps, then the midpoint update with extrapolated h
+# (Section 3.1); their time step from the AB2/AB3 stability regions (Section 3.2).
+MULTISTEP = {
+    "mpea_1d": ("c1_1d", dict(n_macro=(16, 1, 1), box_n=81, micro_steps=120, alpha_micro=0.1, micro_stepper=3)),
+    "mpe_2d": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=24, micro_steps=60, micro_stepper=2)),
+    "mpea_2d_low_damping": ("c5_sweep", dict(n_macro=(6, 6, 1), box_n=48, micro_steps=60, alpha_micro=0.01,
+                                             micro_stepper=3)),
+    "mpea_2d_order2": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=25, micro_steps=50, stencil_order=2, micro_stepper=3)),
+    "mpea_3d": ("c4_3d", dict(n_macro=(5, 5, 5), box_n=16, mu_over_eps=0.9, micro_steps=30, micro_stepper=3)),
+    "mpea_startup_only": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=24, micro_steps=2, micro_stepper=3)),
+    "mpe_three_steps": ("c2_2d", dict(n_macro=(6, 5, 1), box_n=24, micro_steps=3, micro_stepper=2)),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(MULTISTEP))
+def test_multistep_micro_steppers(torch_cuda, case, precision):
+    name, over = MULTISTEP[case]
+    cfg = W.config(name, **over)
+    M0 = W.initial_field(cfg)
+    Hg, info = gpu_micro(torch_cuda, cfg, M0, precision)
+    pts = sorted(set([0, 1, cfg.n_points // 2, cfg.n_points - 1]))
+    Hr = O.micro_batch(cfg, M0, points=pts, dtype=np.longdouble if precision == 0 else np.float64)
+    e = rel_err(Hg[:, pts], Hr)
+    assert e < TOL[precision], (case, precision, e)
+    for p in (0, cfg.n_points - 1):
+        geo = O.box_geometry(cfg, p)
+        assert abs(info["dt"][p] / geo["dt"] - 1) < 1e-12   # the AB2/AB3 stability rule, host vs oracle
+
+
+def test_multistep_not_resident(torch_cuda):
+    from paper_2108_09463_gb300 import HMM, HmmError
+    cfg = W.config("c2_2d", n_macro=(5, 5, 1), box_n=32, micro_steps=10, micro_stepper=3)
+    with pytest.raises(HmmError) as ei:
+        HMM(cfg, precision=1, kernel_variant=2)
+    assert ei.value.status == 1
+
+
 def test_rk4p_3d_not_resident(torch_cuda):
     from paper_2108_09463_gb300 import HMM, HmmError
     cfg = W.config("c4_3d", n_macro=(5, 5, 5), box_n=32, micro_steps=10, micro_stepper=1)

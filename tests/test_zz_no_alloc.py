@@ -6,7 +6,7 @@ applications whose device memory another framework has reserved). It must give
 the same H_avg as the regular entry point, call after call, although every call
 reuses one fixed scratch array inside the library: in 2D, in 3D with boxes so
 large that only a few per-CTA arenas fit the array (a reduced grid whose CTAs
-index the arenas by block), and in 1D with the RK4P micro stepper.
+index the arenas by block), in 1D with the RK4P micro stepper and in 2D with MPEA.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
@@ -97,6 +97,12 @@ def test_noalloc_3d_reduced_grid(torch_cuda):
 def test_noalloc_1d_rk4p(torch_cuda):
     cfg = W.config("c1_1d", n_macro=(16, 1, 1), micro_steps=100, micro_stepper=1)
     _compare_twice(torch_cuda, cfg, (31, 32))
+
+
+def test_noalloc_2d_mpea(torch_cuda):
+    # the multi-step stepper's per-node history arrays enlarge each arena
+    cfg = W.config("c2_2d", n_macro=(6, 6, 1), box_n=32, micro_steps=40, alpha_micro=0.1, micro_stepper=3)
+    _compare_twice(torch_cuda, cfg, (33, 34), kernel_variant=1)
 
 
 def test_noalloc_refuses_a_capturing_stream(torch_cuda):
