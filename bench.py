@@ -491,7 +491,7 @@ def run_micro_only(args, local_rank):
     rec = {"mode": "micro-only", "workload": args.workload, "boxes": cfg.n_points,
            "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
            "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3), "ms": ms,
-           "micro_stepper": ["HeunP", "RK4P"][cfg.micro_stepper], "model": ["field", "flux"][cfg.model],
+           "micro_stepper": ["HeunP", "RK4P", "MPE", "MPEA"][cfg.micro_stepper], "model": ["field", "flux"][cfg.model],
            "micro_dt_mean": float(h.box_info()["dt"].mean()), "micro_steps": cfg.micro_steps}
     if args.cpu_baseline_micro:
         # the oracle on a spread sample of the same boxes, spawned processes on the host cores
@@ -672,7 +672,8 @@ def main():
     ap.add_argument("--alpha-micro", type=float, default=None)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--variant", type=int, default=0, help="FP32 kernel: 0 automatic, 1 generic, 2 resident")
-    ap.add_argument("--micro-stepper", type=int, default=0, help="with --micro-only: 0 HeunP, 1 RK4P")
+    ap.add_argument("--micro-stepper", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="with --micro-only: 0 HeunP, 1 RK4P, 2 MPE, 3 MPEA")
     ap.add_argument("--model", type=int, default=0, help="with --micro-only: 0 field model, 1 flux model (FP64)")
     ap.add_argument("--cpu-baseline-micro", action="store_true",
                     help="with --micro-only: also time the oracle on a sample of the boxes")
