@@ -1,12 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark of the HMM micro-problem path on GB300.
 
-A step is one full HMM macro step (MPEA, Section 3.1) of the field model on the
-3D workload at its full size: a 64^3 periodic macro grid, one 32^3-node micro
-box per macro point (262,144 micro problems), 300 HeunP micro steps each,
+The headline workload is the field model's HMM (MPEA macro steps, Section 3.1)
+on the 3D workload at its full size: a 64^3 periodic macro grid, one 32^3-node
+micro box per macro point (262,144 micro problems), 300 HeunP micro steps each,
 eps = 1/100, a = 1 + 0.5 sin(2 pi y1) sin(2 pi y2) sin(2 pi y3), alpha = 0.1,
-alpha_micro = 1.2, 4th-order stencil: 1.38e12 lattice updates per step. The
-headline value is micro lattice updates per second of the batched FP32 form;
+alpha_micro = 1.2, 4th-order stencil: 1.38e12 lattice updates per macro step.
+Each macro step is taken in 16 waves (hmm_macro_step_wave), and a benchmark
+step is one wave: the micro batch of 16,384 of the boxes (8.6e10 lattice
+updates), the wave that ends a macro step adding the MPEA update of every
+point. The headline value is micro lattice updates per second of the batched FP32 form;
 the plain FP64 method is timed on a sample of the same boxes. The line carries
 the same measurements for the uneven 2D workload (256^2 macro grid, boxes of
 32^2 to 96^2) and the 128^2 2D workload as sub-objects.
@@ -56,7 +59,7 @@ WORKLOADS = {
               "alpha=0.1, alpha_micro=1.2"),
         kernel="micro_fp32_3d_col_kernel<3> (z-column, shared-memory resident, 9-CTA clusters)",
         traffic="micro_fp32_3d_col_c4_traffic.txt", source="micro_fp32_3d_col.cuh",
-        steps=1, e2e_steps=1, fp64_sample=4096),
+        steps=16, waves=16, e2e_steps=1, fp64_sample=4096),
     "c3_2d_uneven": dict(
         desc=("2D HMM, 256^2 macro grid, 65536 uneven micro boxes of 32^2 to 96^2 nodes (eps_i in "
               "[1/400, 1/100], 8 per eps_i), 400 HeunP micro steps, a=1.1+0.25sin(2pi y1)cos(2pi y2)"
@@ -248,7 +251,12 @@ def measure_workload(name, steps, warmup, flush, world=1, dist=None, pool=None, 
     (value = lattice updates/s over the timed steps), the dominant kernel's time per
     launch from the library's events on its stream, the roofline, end to end through
     the host-buffer entry point, the FP64 method on a sample of the same boxes, and
-    the oracle on a bounded sample of boxes (spawned processes on the host cores)."""
+    the oracle on a bounded sample of boxes (spawned processes on the host cores).
+
+    A workload with `waves` > 1 takes each macro step in that many calls of
+    hmm_macro_step_wave (one step = one wave: the micro batch of 1/waves of the
+    boxes; the wave that ends a macro step adds the MPEA update of every point),
+    and the dominant kernel's time is the mean of the timed waves' micro batches."""
     import numpy as np
     import torch
     import workloads as W
@@ -264,36 +272,60 @@ def measure_workload(name, steps, warmup, flush, world=1, dist=None, pool=None, 
     hist = torch.zeros((2, 3, cfg.n_points), dtype=torch.float64, device="cuda")
     h32.set_state(hist, 2)
     M = torch.from_numpy(M0).cuda()
+    nw = spec.get("waves", 1)
+    if nw > 1:
+        # every wave holds the same number of equal boxes, so a step is lu_batch / nw
+        assert cfg.box_n_field is None and cfg.eps_field is None and cfg.n_points % nw == 0
+    lu_step = lu_batch / nw
+    wave = [0, 0, []]    # next wave, macro steps completed in the timed region, wave kernel ms
+
+    def one_step(timed):
+        if nw == 1:
+            h32.macro_step(M, 1)
+            return
+        h32.macro_step_wave(M, wave[0], nw)
+        if timed:
+            wave[2].append(h32.stats()[1])
+            wave[1] += wave[0] == nw - 1
+        wave[0] = (wave[0] + 1) % nw
+
     for _ in range(warmup):
-        h32.macro_step(M, 1)
+        one_step(False)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ms = _timed(lambda: h32.macro_step(M, 1), steps, flush)
+        ms = _timed(lambda: one_step(True), steps, flush)
     torch.cuda.synchronize()
-    ms_max, value = aggregate_ranks(ms, world, steps, lu_batch, dist, "cuda")
-    # the dominant kernel: one micro batch, timed per launch on the library's stream
-    H = torch.empty_like(M)
-    kms = []
-    # (one launch when a step takes more than 10 s: its time is already a long average)
-    for _ in range(kernel_reps if ms / steps < 1e4 else 1):
-        flush.zero_()
-        h32.micro_batch(M, H)
-        kms.append(h32.stats()[1])
-    k_ms = min(kms)
+    ms_max, value = aggregate_ranks(ms, world, steps, lu_step, dist, "cuda")
+    if nw > 1:
+        # the dominant kernel: the timed waves' micro batches, each timed on the
+        # library's stream by its own events
+        k_ms = sum(wave[2]) / len(wave[2])
+        launches = steps * sum(1 for ln in plan.splitlines() if ln.startswith("3D")) + 2 * wave[1]
+    else:
+        # the dominant kernel: one micro batch, timed per launch on the library's stream
+        H = torch.empty_like(M)
+        kms = []
+        # (one launch when a step takes more than 10 s: its time is already a long average)
+        for _ in range(kernel_reps if ms / steps < 1e4 else 1):
+            flush.zero_()
+            h32.micro_batch(M, H)
+            kms.append(h32.stats()[1])
+        k_ms = min(kms)
+        launches = 3 * steps
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     alu_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flops = FLOPS_PER_LU[cfg.dim] * lu_batch
+    flops = FLOPS_PER_LU[cfg.dim] * lu_step
     achieved = flops / (k_ms / 1e3) / 1e12
     hbm = peaks.get("hbm_gbs", 6800.0)
     traffic = None
     if spec["traffic"]:
         traffic = _traffic_from_profile(os.path.join(ROOT, "profiles", spec["traffic"]),
                                         os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", spec["source"]))
-    stream_gbs = BYTES_PER_LU_FP32 * lu_batch / (k_ms / 1e3) / 1e9
+    stream_gbs = BYTES_PER_LU_FP32 * lu_step / (k_ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": traffic, "kernel": spec["kernel"], "kernel_ms": k_ms,
                 "flops_per_lu": FLOPS_PER_LU[cfg.dim],
@@ -339,13 +371,14 @@ def measure_workload(name, steps, warmup, flush, world=1, dist=None, pool=None, 
     h64.close()
     h32.close()
     out = {"workload": spec["desc"], "name": name, "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
-           "ms_per_step": ms_max / steps, "macro_steps_per_s": steps / (ms_max / 1e3), "lu_per_step": lu_batch,
+           "ms_per_step": ms_max / steps, "macro_steps_per_s": steps / nw / (ms_max / 1e3), "lu_per_step": lu_step,
+           "waves_per_macro_step": nw, "lu_per_macro_step": lu_batch,
            "boxes": cfg.n_points, "micro_steps": cfg.micro_steps,
            "fp64_plain": {"value": lu64, "unit": UNIT, "how": fp64_desc, "kernel_ms": ms64},
            "speedup_fp32_vs_fp64": value / world / lu64,
            "fp32_vs_fp64_rel_err": rel,
            "roofline": roofline, "e2e": e2e, "plan": plan,
-           "gpu_launches_per_step": 3, "clocks": clk.summary()}
+           "gpu_launches": launches, "clocks": clk.summary()}
     if pool is not None:
         oracle_sample(name, 1, cpu_workers, pool)   # each worker generates the seeded input once, untimed
         v, sinfo = oracle_sample(name, cpu_boxes_per_worker, cpu_workers, pool)
@@ -427,8 +460,13 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": spec["desc"], "name": args.headline, "boxes": head["boxes"],
                        "micro_steps": head["micro_steps"], "lu_per_step": head["lu_per_step"],
                        "precision": "fp32-batched",
-                       "step": "one MPEA macro step (one micro batch over every box + the MPEA update), "
-                               "from a restart state",
+                       "step": ("one MPEA macro step (one micro batch over every box + the MPEA update), "
+                                "from a restart state" if head["waves_per_macro_step"] == 1 else
+                                f"one wave of an MPEA macro step taken in {head['waves_per_macro_step']} waves "
+                                f"(hmm_macro_step_wave): the micro batch of {head['boxes'] // head['waves_per_macro_step']} "
+                                f"of the {head['boxes']} boxes; every {head['waves_per_macro_step']}th wave ends the "
+                                "macro step with the MPEA update of every point; from a restart state"),
+                       "lu_per_macro_step": head["lu_per_macro_step"],
                        "l2": "flushed (256 MB write) between timed steps; the working set is larger than L2",
                        "parallelism": f"replicas x{world}"},
             "macro_steps_per_s": head["macro_steps_per_s"],
@@ -437,7 +475,7 @@ def run_ours(args, rank, world, local_rank):
             "fp32_vs_fp64_rel_err": head["fp32_vs_fp64_rel_err"],
             "roofline": head["roofline"], "cpu_baseline": head["cpu_baseline"], "e2e": head["e2e"],
             "clocks": clocks,
-            "gpu_launches": head["gpu_launches_per_step"] * steps,
+            "gpu_launches": head["gpu_launches"],
             "plan": head["plan"],
             "workloads": subs,
             "dns": dns,
@@ -652,7 +690,8 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed macro steps of the headline workload (default: 1 for the 3D workload)")
+                    help="timed steps of the headline workload (default: 16 for the 3D workload, whose step "
+                         "is one of the 16 waves of a macro step)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)

@@ -207,6 +207,28 @@ hmm_status hmm_macro_step(void* handle, double* M_dev, int n_steps);
 /* As hmm_macro_step with M in host memory (copied in and out once per call). */
 hmm_status hmm_macro_step_host(void* handle, double* M_host, int n_steps);
 
+/* One MPEA (or MPE) macro step of eq. macro_disc taken in n_waves calls, for
+ * batches whose micro problems are too many to solve in one call of bounded
+ * length. The micro problems are independent (Section 4.4), so the micro batch
+ * of the step is split into n_waves contiguous shares of the handle's work list
+ * (each launch group's items, longest first, or the generic kernel's box list):
+ * call `wave` = 0, 1, ..., n_waves-1 in order with the same M_dev and n_waves.
+ * Each call solves its share's micro problems from M_dev (read only) and keeps
+ * their H_avg (field model) or flux columns (flux model) in the handle; the call
+ * with wave = n_waves-1 then takes the macro update of every point (eqs. h_term,
+ * h_mpea or h_mpe, mpe_update; div F_avg first for the flux model) in place on
+ * M_dev and advances the step count. The n_waves calls together give the same
+ * M_dev and history as hmm_macro_step(handle, M_dev, 1), bit for bit.
+ * Needs the multistep history (step count >= 2 for MPEA, >= 1 for MPE: take the
+ * RK4P start-up steps with hmm_macro_step first); 1 <= n_waves <= the number of
+ * micro problems; HMM_ERR_INVALID_ARG otherwise or when a wave comes out of order.
+ * Any other micro-batch or macro-step call on the handle between two waves, and
+ * hmm_set_state, abandons the step in progress (M_dev is untouched until the
+ * last wave; the next call must be wave 0). Synchronises the library's stream;
+ * hmm_stats' last time is the wave's micro batch. This entry point is an addition
+ * of this library; the paper solves each macro step's micro problems at once. */
+hmm_status hmm_macro_step_wave(void* handle, double* M_dev, int wave, int n_waves);
+
 /* Restart state of the macro stepper: the history hist (2 x 3 x P FP64 device
  * buffer: h^{j-1} then h^{j-2}, eq. h_term; MPE reads only h^{j-1}) and the step
  * count j. The macro field itself is the caller's M. get copies out, set copies in. */

@@ -21,7 +21,7 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 
 # The symbols include/hmm.h declares (checked by the CPU test suite).
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
-            "hmm_macro_step_host", "hmm_get_state", "hmm_set_state", "hmm_stats",
+            "hmm_macro_step_host", "hmm_macro_step_wave", "hmm_get_state", "hmm_set_state", "hmm_stats",
             "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
             "hmm_flux_batch", "hmm_micro_batch_points", "hmm_plan_report", "hmm_last_error", "hmm_destroy")
 # The symbols include/hmm_dns.h declares.
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_micro_batch_points.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int]
     lib.hmm_macro_step.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_macro_step_host.argtypes = [c_void_p, c_void_p, c_int]
+    lib.hmm_macro_step_wave.argtypes = [c_void_p, c_void_p, c_int, c_int]
     lib.hmm_get_state.argtypes = [c_void_p, c_void_p, POINTER(c_longlong)]
     lib.hmm_set_state.argtypes = [c_void_p, c_void_p, c_longlong]
     lib.hmm_stats.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
@@ -281,6 +282,13 @@ class HMM:
 
     def macro_step_host(self, M, n_steps=1):
         self._check(self.lib.hmm_macro_step_host(self.h, c_void_p(_ptr(M)), int(n_steps)))
+        return M
+
+    def macro_step_wave(self, M, wave, n_waves):
+        """Wave `wave` of n_waves of one macro step (hmm_macro_step_wave); the last
+        wave updates M in place."""
+        M = self._field(M)
+        self._check(self.lib.hmm_macro_step_wave(self.h, c_void_p(M.data_ptr()), int(wave), int(n_waves)))
         return M
 
     def get_state(self):

@@ -353,6 +353,10 @@ struct HmmHandle {
   double last_ms = 0;
   cudaGraphExec_t graph = nullptr;
   const double* graph_M = nullptr;
+  // hmm_macro_step_wave: the next wave expected, the wave count and M of the macro
+  // step in progress (wave_next = 0: none)
+  int wave_next = 0, wave_n = 0;
+  const double* wave_M = nullptr;
   std::string err;
   MicroArgs args{};
   // hmm_micro_batch_points: box table and generic-kernel arena of the last subset
@@ -840,8 +844,10 @@ hmm_status build(HmmHandle* h) {
   return HMM_OK;
 }
 
-// Enqueue one micro batch (no synchronisation).
+// Enqueue one micro batch (no synchronisation). It overwrites what a macro step in
+// waves has gathered so far, so it abandons such a step.
 hmm_status enqueue_micro(HmmHandle* h, const double* M, double* Havg) {
+  h->wave_next = 0;
   HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int) * kQueues, h->stream));
   MicroArgs a = h->args;
   a.M = M;
@@ -855,6 +861,41 @@ hmm_status enqueue_micro(HmmHandle* h, const double* M, double* Havg) {
     e = launch_flux_divergence(h->d_F, Havg, h->dim, h->nmac, h->DX, h->p.interp_order, h->P, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "flux divergence launch");
   }
+  return HMM_OK;
+}
+
+// Enqueue the micro batch of wave w of n: a contiguous share of every resident launch
+// group's work items (each group's share keeps its longest-first order), or of the
+// generic kernel's box list. The kernels write H_avg (field model) or F (flux model)
+// at the macro points of the wave's boxes only.
+hmm_status enqueue_micro_wave(HmmHandle* h, const double* M, double* Havg, int w, int n) {
+  HMM_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int) * kQueues, h->stream));
+  MicroArgs a = h->args;
+  a.M = M;
+  a.Havg = Havg;
+  cudaError_t e = cudaSuccess;
+  if (h->res2d) {
+    Res2dPlan pl;
+    pl.smem = h->plan.smem;
+    pl.dim = h->plan.dim;
+    for (const Res2dGroup& g : h->plan.groups) {
+      const long long lo = (long long)g.n_items * w / n, hi = (long long)g.n_items * (w + 1) / n;
+      if (hi == lo) continue;
+      Res2dGroup s = g;
+      s.first_item = g.first_item + (int)lo;
+      s.n_items = (int)(hi - lo);
+      pl.groups.push_back(s);
+    }
+    if (!pl.groups.empty()) e = res2d_launch(a, h->radius, pl, h->d_items, h->d_queue, h->stream);
+  } else {
+    const long long lo = (long long)h->nb * w / n, hi = (long long)h->nb * (w + 1) / n;
+    a.boxes = h->d_boxes + lo;
+    a.n_boxes = (int)(hi - lo);
+    const int grid = std::min(h->grid, a.n_boxes);
+    e = h->p.precision == HMM_FP64_PLAIN ? launch_micro_fp64(a, h->dim, h->radius, grid, h->block, h->smem, h->stream)
+                                         : launch_micro_fp32(a, h->dim, h->radius, grid, h->block, h->smem, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "micro kernel launch");
   return HMM_OK;
 }
 
@@ -1127,6 +1168,51 @@ hmm_status hmm_macro_step_host(void* handle, double* M_host, int n_steps) {
   return HMM_OK;
 }
 
+hmm_status hmm_macro_step_wave(void* handle, double* M_dev, int wave, int n_waves) {
+  HmmHandle* h = as_handle(handle);
+  if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
+  if (!M_dev) return fail(h, HMM_ERR_INVALID_ARG, "null M_dev");
+  if (n_waves < 1 || n_waves > h->nb || wave < 0 || wave >= n_waves)
+    return fail(h, HMM_ERR_INVALID_ARG, "need 1 <= n_waves <= the number of micro problems and 0 <= wave < n_waves");
+  if (h->j < (h->p.macro_stepper == HMM_MPE ? 1 : 2))
+    return fail(h, HMM_ERR_INVALID_ARG,
+                "a macro step in waves needs the multistep history: take the RK4P start-up steps with hmm_macro_step");
+  if (wave != h->wave_next || (wave > 0 && (n_waves != h->wave_n || M_dev != h->wave_M)))
+    return fail(h, HMM_ERR_INVALID_ARG,
+                "the waves of one macro step come in the order 0 .. n_waves-1, with the same n_waves and M_dev");
+  h->wave_next = 0;
+  HMM_TRY(begin_call(h));
+  HMM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  hmm_status s = enqueue_micro_wave(h, M_dev, h->d_H, wave, n_waves);
+  if (s != HMM_OK) return s;
+  HMM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  const bool last = wave == n_waves - 1;
+  if (last) {
+    cudaError_t e = cudaSuccess;
+    if (h->p.model == HMM_FLUX_MODEL)
+      e = launch_flux_divergence(h->d_F, h->d_H, h->dim, h->nmac, h->DX, h->p.interp_order, h->P, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "flux divergence launch");
+    e = launch_mpea_update(M_dev, h->d_H, h->d_hist, h->p.alpha, h->dt_macro, h->p.macro_stepper, h->P, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mpea kernel launch");
+    e = launch_check_finite(M_dev, 3 * h->P, h->d_err, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "finite check launch");
+  }
+  HMM_TRY(end_call(h));
+  s = check_error_word(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->last_ms = ms;
+  if (s != HMM_OK) return s;
+  if (last) {
+    h->j += 1;
+  } else {
+    h->wave_next = wave + 1;
+    h->wave_n = n_waves;
+    h->wave_M = M_dev;
+  }
+  return HMM_OK;
+}
+
 hmm_status hmm_get_state(void* handle, double* hist_dev, long long* j) {
   HmmHandle* h = as_handle(handle);
   if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
@@ -1144,6 +1230,7 @@ hmm_status hmm_set_state(void* handle, const double* hist_dev, long long j) {
   HmmHandle* h = as_handle(handle);
   if (!h) return fail(nullptr, HMM_ERR_NOT_INITIALISED, "null handle");
   if (j < 0) return fail(h, HMM_ERR_INVALID_ARG, "negative step count");
+  h->wave_next = 0;
   if (hist_dev) {
     HMM_TRY(begin_call(h));
     HMM_CUDA(h, cudaMemcpyAsync(h->d_hist, hist_dev, sizeof(double) * 6 * (size_t)h->P,

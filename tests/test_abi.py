@@ -123,6 +123,7 @@ def test_null_arguments(lib):
     assert lib.hmm_init(None, None, None) == 1
     assert lib.hmm_micro_batch(None, None, None) == 7
     assert lib.hmm_macro_step(None, None, 1) == 7
+    assert lib.hmm_macro_step_wave(None, None, 0, 1) == 7
     lib.hmm_destroy(None)
 
 

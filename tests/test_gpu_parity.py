@@ -550,6 +550,75 @@ def test_graph_replay_equals_single_steps(torch_cuda):
     assert torch_cuda.equal(Ma, Mb)
 
 
+# Macro steps in waves (hmm_macro_step_wave): each micro problem is solved by the same
+# kernel instance from the same M whichever wave holds it, so n_waves calls must give
+# hmm_macro_step's M and history bit for bit.
+WAVES = {
+    "2d_resident": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=20), 1, {}),
+    "2d_uneven": ("c3_2d_uneven", dict(n_macro=(12, 12, 1), micro_steps=12), 1, {}),
+    "2d_generic_fp64": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=20), 0, {}),
+    "3d_zcolumn": ("c4_3d", dict(n_macro=(6, 6, 6), micro_steps=6), 1, {}),
+    "2d_flux_mpe": ("c2_2d", dict(n_macro=(8, 8, 1), box_n=24, micro_steps=20, model=1, macro_stepper=1), 1, {}),
+}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", sorted(WAVES))
+def test_macro_step_in_waves_equals_macro_step(torch_cuda, case):
+    from paper_2108_09463_gb300 import HMM
+    name, over, precision, _ = WAVES[case]
+    cfg = W.config(name, **over)
+    M0 = torch_cuda.from_numpy(W.initial_field(cfg)).cuda()
+    a, b = HMM(cfg, precision=precision), HMM(cfg, precision=precision)
+    Ma, Mb = M0.clone(), M0.clone()
+    start = 1 if getattr(cfg, "macro_stepper", 0) == 1 else 2
+    a.macro_step(Ma, start)
+    b.macro_step(Mb, start)
+    for n_waves in (1, 5, 7):
+        a.macro_step(Ma, 1)
+        for w in range(n_waves):
+            before = Mb.clone()
+            b.macro_step_wave(Mb, w, n_waves)
+            if w < n_waves - 1:
+                assert torch_cuda.equal(Mb, before)   # M changes only at the last wave
+        assert torch_cuda.equal(Ma, Mb), n_waves
+        ha, ja = a.get_state()
+        hb, jb = b.get_state()
+        assert ja == jb and torch_cuda.equal(ha, hb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.gpu
+def test_macro_step_in_waves_refusals(torch_cuda):
+    from paper_2108_09463_gb300 import HMM, HmmError
+    cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=10)
+    M = torch_cuda.from_numpy(W.initial_field(cfg)).cuda()
+    h = HMM(cfg, precision=1)
+    with pytest.raises(HmmError, match="start-up"):          # no MPEA history yet
+        h.macro_step_wave(M, 0, 2)
+    h.macro_step(M, 2)
+    for wave, n in ((1, 2), (0, 0), (2, 2), (0, 65)):         # out of order or out of range
+        with pytest.raises(HmmError) as ei:
+            h.macro_step_wave(M, wave, n)
+        assert ei.value.status == 1
+    h.macro_step_wave(M, 0, 3)
+    with pytest.raises(HmmError, match="order"):
+        h.macro_step_wave(M, 2, 3)                            # wave 1 skipped
+    with pytest.raises(HmmError, match="order"):
+        h.macro_step_wave(M.clone(), 1, 3)                    # another M
+    h.macro_step_wave(M, 1, 3)
+    h.micro_batch(M)                                          # abandons the step in progress
+    with pytest.raises(HmmError, match="order"):
+        h.macro_step_wave(M, 2, 3)
+    _, j = h.get_state()
+    assert j == 2
+    for w in range(3):
+        h.macro_step_wave(M, w, 3)
+    assert h.get_state()[1] == 3
+    h.close()
+
+
 def test_host_entry_points(torch_cuda):
     from paper_2108_09463_gb300 import HMM
     cfg = W.config("c2_2d", n_macro=(8, 8, 1), box_n=24, micro_steps=20)
