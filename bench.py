@@ -325,6 +325,8 @@ def measure_workload(name, steps, warmup, flush, world=1, dist=None, pool=None, 
     if spec["traffic"]:
         traffic = _traffic_from_profile(os.path.join(ROOT, "profiles", spec["traffic"]),
                                         os.path.join(ROOT, "paper_2108_09463_gb300", "csrc", spec["source"]))
+        if traffic is not None:
+            traffic /= nw   # recorded per launch over every box; a wave's launch holds 1/nw of them
     stream_gbs = BYTES_PER_LU_FP32 * lu_step / (k_ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": traffic, "kernel": spec["kernel"], "kernel_ms": k_ms,
@@ -542,16 +544,22 @@ def run_micro_only(args, local_rank):
     if args.macro_steps > 0:
         # steady-state macro steps (MPEA, one micro batch each, graph replay) after
         # the RK4P start-up steps j = 0, 1 and one warm-up step
+        # (--waves n: each timed macro step in n calls of hmm_macro_step_wave)
         h.macro_step(M, 3)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
-        h.macro_step(M, args.macro_steps)
+        if args.waves > 1:
+            for _ in range(args.macro_steps):
+                for w in range(args.waves):
+                    h.macro_step_wave(M, w, args.waves)
+        else:
+            h.macro_step(M, args.macro_steps)
         t1.record()
         torch.cuda.synchronize()
         sec = t0.elapsed_time(t1) / 1e3
-        rec.update(macro_steps=args.macro_steps, macro_steps_per_s=args.macro_steps / sec)
+        rec.update(macro_steps=args.macro_steps, macro_steps_per_s=args.macro_steps / sec, waves=args.waves)
     h.close()
     print(json.dumps(rec), flush=True)
 
@@ -721,6 +729,8 @@ def main():
     ap.add_argument("--dns", action="store_true",
                     help="time the direct simulation (--workload dns_*, --macro-grid for its grid, "
                          "--steps MPEA steps, --fp64-steps for the FP64 form)")
+    ap.add_argument("--waves", type=int, default=1,
+                    help="with --micro-only --macro-steps: take each timed macro step in this many waves")
     ap.add_argument("--macro-steps", type=int, default=0,
                     help="with --micro-only: also time this many steady-state macro steps")
     args = ap.parse_args()
