@@ -532,7 +532,8 @@ def run_micro_only(args, local_rank):
            "precision": args.precision, "variant": args.variant, "lu_per_batch": lu,
            "ms_per_batch": sum(ms) / len(ms), "LU_per_s": lu / (sum(ms) / len(ms) / 1e3), "ms": ms,
            "micro_stepper": ["HeunP", "RK4P", "MPE", "MPEA"][cfg.micro_stepper], "model": ["field", "flux"][cfg.model],
-           "micro_dt_mean": float(h.box_info()["dt"].mean()), "micro_steps": cfg.micro_steps}
+           "micro_dt_mean": float(h.box_info()["dt"].mean()), "micro_steps": cfg.micro_steps,
+           "plan": h.plan_report().strip()}
     if args.cpu_baseline_micro:
         # the oracle on a spread sample of the same boxes, spawned processes on the host cores
         import multiprocessing as mp
