@@ -307,6 +307,16 @@ hmm_status hmm_micro_batch_noalloc(const hmm_params* params, const double* M_dev
  * of this library; the paper has no counterpart. */
 const char* hmm_plan_report(void* handle);
 
+/* The current device's FP32 fused multiply-add rate in flop/s (an FMA = 2 flops),
+ * measured: a kernel that fills every SM runs eight independent FMA chains per
+ * thread for a few milliseconds, as scalar FP32 FMAs (packed = 0) or as the paired
+ * FP32x2 FMAs that the micro kernels issue (packed = 1), timed with CUDA events on a
+ * stream of its own (synchronised before returning). A denominator for the roofline
+ * of the FP32 micro kernels, which are bound by instruction issue rather than by
+ * memory; the paper has no counterpart. HMM_ERR_INVALID_ARG for a null output or
+ * packed not 0/1; HMM_ERR_CUDA if a CUDA call fails (hmm_last_error(NULL) says so). */
+hmm_status hmm_fp32_fma_rate(int packed, double* flops_per_s);
+
 /* One-line description of the last failure on this handle ("" if none). Valid
  * until the next call on the handle. NULL handle: the last hmm_init failure. */
 const char* hmm_last_error(void* handle);

@@ -23,7 +23,8 @@ HMM_FP64_PLAIN, HMM_FP32_BATCHED = 0, 1
 EXPORTED = ("hmm_init", "hmm_micro_batch", "hmm_micro_batch_host", "hmm_macro_step",
             "hmm_macro_step_host", "hmm_macro_step_wave", "hmm_get_state", "hmm_set_state", "hmm_stats",
             "hmm_box_info", "hmm_set_face_table", "hmm_macro_dt", "hmm_micro_batch_noalloc",
-            "hmm_flux_batch", "hmm_micro_batch_points", "hmm_plan_report", "hmm_last_error", "hmm_destroy")
+            "hmm_flux_batch", "hmm_micro_batch_points", "hmm_plan_report", "hmm_fp32_fma_rate", "hmm_last_error",
+            "hmm_destroy")
 # The symbols include/hmm_dns.h declares.
 EXPORTED_DNS = ("hmm_dns_init", "hmm_dns_set_face_table", "hmm_dns_step", "hmm_dns_step_host",
                 "hmm_dns_reset", "hmm_dns_info", "hmm_dns_plan", "hmm_dns_last_error", "hmm_dns_destroy")
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hmm_macro_step.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_macro_step_host.argtypes = [c_void_p, c_void_p, c_int]
     lib.hmm_macro_step_wave.argtypes = [c_void_p, c_void_p, c_int, c_int]
+    lib.hmm_fp32_fma_rate.argtypes = [c_int, ctypes.POINTER(c_double)]
     lib.hmm_get_state.argtypes = [c_void_p, c_void_p, POINTER(c_longlong)]
     lib.hmm_set_state.argtypes = [c_void_p, c_void_p, c_longlong]
     lib.hmm_stats.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
@@ -334,6 +336,17 @@ class HMM:
             self.close()
         except Exception:
             pass
+
+
+def fp32_fma_rate(packed=True):
+    """The current device's FP32 FMA rate in flop/s (hmm_fp32_fma_rate): paired
+    FP32x2 FMAs (packed) or scalar FMAs."""
+    lib = load_library()
+    r = c_double()
+    st = lib.hmm_fp32_fma_rate(1 if packed else 0, ctypes.byref(r))
+    if st != HMM_OK:
+        raise HmmError(st, lib.hmm_last_error(None).decode())
+    return r.value
 
 
 def micro_batch_noalloc(cfg, M, out, stream=None):

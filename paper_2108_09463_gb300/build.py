@@ -28,7 +28,7 @@ LIB = os.path.join(HERE, "libhmm_gb300.so")
 STAMP = LIB + ".sha256"
 SOURCES = ["hmm_api.cu", "macro.cu", "micro_fp64.cu", "micro_fp32.cu", "micro_fp32_2d.cu", "noalloc.cu",
            "res2d_pack.cu", "res2d_cluster_a.cu", "res2d_cluster_b.cu", "res2d_any.cu", "res2d_rk4.cu", "res2d_tr2.cu",
-           "res3d.cu", "dns.cu"]
+           "res3d.cu", "dns.cu", "fma_rate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -124,6 +124,8 @@ def test_null_arguments(lib):
     assert lib.hmm_micro_batch(None, None, None) == 7
     assert lib.hmm_macro_step(None, None, 1) == 7
     assert lib.hmm_macro_step_wave(None, None, 0, 1) == 7
+    assert lib.hmm_fp32_fma_rate(1, None) == 1          # checked before any CUDA call
+    assert lib.hmm_fp32_fma_rate(2, ctypes.byref(ctypes.c_double())) == 1
     lib.hmm_destroy(None)
 
 
