@@ -9,11 +9,16 @@
   parameters (Section 5, locally periodic example: mu = 3.9 eps, mu' = 8 eps,
   eta ~ eps^2, alpha = 1.2) and the separable (EX3) coefficient in 2D.
 * Invariants: constant M gives H_avg = 0; rotating all macro vectors rotates H_avg.
+* The error's dependence on eps (Section 4.4, length of the time interval eta): with
+  mu, mu' and eta large enough that the other contributions are small, the
+  remaining error E_eps of the (EX2) micro problem falls by about four when eps is
+  halved (E_eps <= C eps^2), with A^H from the cell problem.
 """
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import cell_problem as C
 from oracle import hmm_oracle as O
 
 
@@ -183,3 +188,48 @@ def test_rk4p_micro_batch_close_to_heunp():
     cfg1 = cfg1.replace(dt_safety=cfg.dt_safety * dt0 * 240 / (cfg1.micro_steps * dt1))
     H1 = O.micro_batch(cfg1, M0, points=[3, 9])
     assert np.abs(H1 - H0).max() < 1e-3 * np.abs(H0).max(), (H0, H1)
+
+
+def test_ex2_error_falls_as_eps_squared():
+    """(EX2) with alpha_micro = 1: E_avg at eps = 1/50 over E_avg at eps = 1/100.
+
+    Section 4.4 compares the saturated errors of (EX2) for alpha = 1 at two values of
+    eps a factor two apart and finds them a factor of about four apart. Here mu = 3.9
+    eps (the section's averaging width), mu' = 12 eps and eta = 2 eps^2 are large
+    enough that E_mu, E_mu' and E_eta are below E_eps (raising mu' to 14 eps or eta to
+    2.5 eps^2 changes neither error by more than 15 %), and 8 points per eps with the
+    order-4 stencil keep the discretisation error near 6e-6; the grids of the two
+    boxes are identical in units of eps, so only the scale separation differs.
+    """
+    tp = 2 * np.pi
+
+    def a(y1, y2):
+        return (0.5 + (0.5 + 0.25 * np.sin(tp * y1)) * (0.5 + 0.25 * np.sin(tp * y2))
+                + 0.25 * (np.cos(tp * (y1 - y2)) + np.sin(tp * y1)))
+
+    AH = C.homogenised_coefficient_2d(a, 64)
+    # the (EX2) coefficient as sums of separable products of the fast variable:
+    # 0.75 + 0.375 sin y1 + 0.125 sin y2 + 0.3125 sin y1 sin y2 + 0.25 cos y1 cos y2
+    terms = [W._term(0.375, W._sin(0)), W._term(0.125, W._sin(1)), W._term(0.3125, W._sin(0), W._sin(1)),
+             W._term(0.25, W._cos(0), W._cos(1))]
+    y = np.random.default_rng(5).random((2, 64))
+    expanded = (0.75 + 0.375 * np.sin(tp * y[0]) + 0.125 * np.sin(tp * y[1])
+                + 0.3125 * np.sin(tp * y[0]) * np.sin(tp * y[1]) + 0.25 * np.cos(tp * y[0]) * np.cos(tp * y[1]))
+    np.testing.assert_allclose(expanded, a(y[0], y[1]), atol=1e-15)
+    K, mup, eta = 8, 12.0, 2.0
+    err = {}
+    for inv_eps in (50, 100):
+        eps = 1.0 / inv_eps
+        cfg = W.HMMConfig(dim=2, n_macro=(24, 24, 1), alpha=0.01, alpha_micro=1.0, c0=0.75, terms=terms, eps=eps,
+                          box_n=int(round(2 * mup * K)) + 1, pts_per_eps=K, micro_steps=10, mu_over_eps=3.9)
+        dt = O.micro_dt(cfg, eps / K)
+        cfg = cfg.replace(micro_steps=int(np.ceil(eta * eps * eps / dt)))
+        X1, X2 = np.meshgrid(*W.macro_coords(cfg), indexing="ij")
+        M0 = W.ex2_initial(X1, X2).reshape(3, -1)
+        p = 7 * 24 + 3
+        H = O.micro_batch(cfg, M0, points=[p])[:, 0]
+        _, _, Q2 = O.q_derivatives_at_centre(cfg, M0, p)
+        tgt = O.homogenised_target(AH, Q2)
+        err[inv_eps] = np.linalg.norm(H - tgt) / np.linalg.norm(tgt)
+    assert err[50] < 5e-4 and err[100] < 2e-4, err
+    assert 3.2 < err[50] / err[100] < 5.0, err
