@@ -12,7 +12,9 @@
 * The error's dependence on eps (Section 4.4, length of the time interval eta): with
   mu, mu' and eta large enough that the other contributions are small, the
   remaining error E_eps of the (EX2) micro problem falls by about four when eps is
-  halved (E_eps <= C eps^2), with A^H from the cell problem.
+  halved (E_eps <= C eps^2), with A^H from the cell problem; and on the averaging
+  width mu (Section 4.4, averaging domain size): steep while mu is a few eps, flat
+  from about 3.5 eps.
 """
 import numpy as np
 import pytest
@@ -190,17 +192,9 @@ def test_rk4p_micro_batch_close_to_heunp():
     assert np.abs(H1 - H0).max() < 1e-3 * np.abs(H0).max(), (H0, H1)
 
 
-def test_ex2_error_falls_as_eps_squared():
-    """(EX2) with alpha_micro = 1: E_avg at eps = 1/50 over E_avg at eps = 1/100.
-
-    Section 4.4 compares the saturated errors of (EX2) for alpha = 1 at two values of
-    eps a factor two apart and finds them a factor of about four apart. Here mu = 3.9
-    eps (the section's averaging width), mu' = 12 eps and eta = 2 eps^2 are large
-    enough that E_mu, E_mu' and E_eta are below E_eps (raising mu' to 14 eps or eta to
-    2.5 eps^2 changes neither error by more than 15 %), and 8 points per eps with the
-    order-4 stencil keep the discretisation error near 6e-6; the grids of the two
-    boxes are identical in units of eps, so only the scale separation differs.
-    """
+def _ex2_error(inv_eps, mu_over_eps, K=8, mup=12.0, eta=2.0):
+    """Relative E_avg of the (EX2) micro problem at one macro point, alpha_micro = 1,
+    against A^H from the cell problem; mu', eta in units of eps and eps^2."""
     tp = 2 * np.pi
 
     def a(y1, y2):
@@ -216,20 +210,44 @@ def test_ex2_error_falls_as_eps_squared():
     expanded = (0.75 + 0.375 * np.sin(tp * y[0]) + 0.125 * np.sin(tp * y[1])
                 + 0.3125 * np.sin(tp * y[0]) * np.sin(tp * y[1]) + 0.25 * np.cos(tp * y[0]) * np.cos(tp * y[1]))
     np.testing.assert_allclose(expanded, a(y[0], y[1]), atol=1e-15)
-    K, mup, eta = 8, 12.0, 2.0
-    err = {}
-    for inv_eps in (50, 100):
-        eps = 1.0 / inv_eps
-        cfg = W.HMMConfig(dim=2, n_macro=(24, 24, 1), alpha=0.01, alpha_micro=1.0, c0=0.75, terms=terms, eps=eps,
-                          box_n=int(round(2 * mup * K)) + 1, pts_per_eps=K, micro_steps=10, mu_over_eps=3.9)
-        dt = O.micro_dt(cfg, eps / K)
-        cfg = cfg.replace(micro_steps=int(np.ceil(eta * eps * eps / dt)))
-        X1, X2 = np.meshgrid(*W.macro_coords(cfg), indexing="ij")
-        M0 = W.ex2_initial(X1, X2).reshape(3, -1)
-        p = 7 * 24 + 3
-        H = O.micro_batch(cfg, M0, points=[p])[:, 0]
-        _, _, Q2 = O.q_derivatives_at_centre(cfg, M0, p)
-        tgt = O.homogenised_target(AH, Q2)
-        err[inv_eps] = np.linalg.norm(H - tgt) / np.linalg.norm(tgt)
+    eps = 1.0 / inv_eps
+    cfg = W.HMMConfig(dim=2, n_macro=(24, 24, 1), alpha=0.01, alpha_micro=1.0, c0=0.75, terms=terms, eps=eps,
+                      box_n=int(round(2 * mup * K)) + 1, pts_per_eps=K, micro_steps=10, mu_over_eps=mu_over_eps)
+    dt = O.micro_dt(cfg, eps / K)
+    cfg = cfg.replace(micro_steps=int(np.ceil(eta * eps * eps / dt)))
+    X1, X2 = np.meshgrid(*W.macro_coords(cfg), indexing="ij")
+    M0 = W.ex2_initial(X1, X2).reshape(3, -1)
+    p = 7 * 24 + 3
+    H = O.micro_batch(cfg, M0, points=[p])[:, 0]
+    _, _, Q2 = O.q_derivatives_at_centre(cfg, M0, p)
+    tgt = O.homogenised_target(AH, Q2)
+    return np.linalg.norm(H - tgt) / np.linalg.norm(tgt)
+
+
+def test_ex2_error_falls_as_eps_squared():
+    """(EX2) with alpha_micro = 1: E_avg at eps = 1/50 over E_avg at eps = 1/100.
+
+    Section 4.4 compares the saturated errors of (EX2) for alpha = 1 at two values of
+    eps a factor two apart and finds them a factor of about four apart. Here mu = 3.9
+    eps (the section's averaging width), mu' = 12 eps and eta = 2 eps^2 are large
+    enough that E_mu, E_mu' and E_eta are below E_eps (raising mu' to 14 eps or eta to
+    2.5 eps^2 changes neither error by more than 15 %), and 8 points per eps with the
+    order-4 stencil keep the discretisation error near 6e-6; the grids of the two
+    boxes are identical in units of eps, so only the scale separation differs.
+    """
+    err = {inv_eps: _ex2_error(inv_eps, 3.9) for inv_eps in (50, 100)}
     assert err[50] < 5e-4 and err[100] < 2e-4, err
     assert 3.2 < err[50] / err[100] < 5.0, err
+
+
+def test_ex2_error_against_averaging_width():
+    """(EX2), eps = 1/100: E_avg against the averaging half-width mu (Section 4.4,
+    averaging domain size). The bound E_mu <= C (mu^(px+1) + (eps/mu)^(qx+2)) with
+    qx = 7 makes the error fall steeply while mu is a few eps, and the section finds
+    it flat once mu is about 3.5 eps (the other terms then dominate): measured 2.4e-3
+    at mu = 2 eps, 5.0e-5 at 3.5 eps and 5.3e-5 at 4.5 eps.
+    """
+    e2, e35, e45 = (_ex2_error(100, mu) for mu in (2.0, 3.5, 4.5))
+    assert e2 > 20 * e35, (e2, e35)
+    assert abs(e45 - e35) < 0.2 * e35, (e35, e45)
+    assert e35 < 1e-4
