@@ -313,8 +313,10 @@ const char* hmm_plan_report(void* handle);
  * FP32x2 FMAs that the micro kernels issue (packed = 1), timed with CUDA events on a
  * stream of its own (synchronised before returning). A denominator for the roofline
  * of the FP32 micro kernels, which are bound by instruction issue rather than by
- * memory; the paper has no counterpart. HMM_ERR_INVALID_ARG for a null output or
- * packed not 0/1; HMM_ERR_CUDA if a CUDA call fails (hmm_last_error(NULL) says so). */
+ * memory; the paper has no counterpart. It allocates one float of device memory
+ * for the duration of the call. HMM_ERR_INVALID_ARG for a null output or packed not
+ * 0/1; HMM_ERR_OUT_OF_MEMORY if that allocation fails; HMM_ERR_CUDA if another CUDA
+ * call fails (hmm_last_error(NULL) says which kind). */
 hmm_status hmm_fp32_fma_rate(int packed, double* flops_per_s);
 
 /* One-line description of the last failure on this handle ("" if none). Valid
