@@ -88,7 +88,8 @@ extern "C" hmm_status hmm_fp32_fma_rate(int packed, double* flops_per_s) {
     *flops_per_s = 2.0 * fmas / (ms * 1e-3);
     s = HMM_OK;
   } while (false);
-  if (s != HMM_OK) set_null_handle_error("hmm_fp32_fma_rate: CUDA call failed");
+  if (s == HMM_ERR_OUT_OF_MEMORY) set_null_handle_error("hmm_fp32_fma_rate: cudaMalloc of the result word failed");
+  else if (s != HMM_OK) set_null_handle_error("hmm_fp32_fma_rate: CUDA call failed");
   else set_null_handle_error("");
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
