@@ -438,6 +438,21 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
       for (int stage = 0; stage < 2; ++stage) {
         const float* src = stage == 0 ? vA : vB;
         const unsigned* rt = rtab + 6 * stage;
+        // The tile's own values of the stage's state and the addresses of the planes beyond
+        // the slab need no barrier (this thread stored the former, the latter are fixed per
+        // box), so they are loaded before it and arrive while it completes.
+        float2 vk[kCol3S][3];
+        unsigned rtl[6];
+        if (active) {
+#pragma unroll
+          for (int k = 0; k < kCol3S; ++k)
+            if (k < S) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) vk[k][c] = lds2(src + c * cstrV + k * PV + rowoff);
+            }
+#pragma unroll
+          for (int e = 0; e < 6; ++e) rtl[e] = rt[e];
+        }
         if (cs > 1) cluster_wait(); else __syncthreads();
         float2 part2[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
         // y and x directions of the stencil at slab plane k (local planes only), v0 the
@@ -487,7 +502,7 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
           float2 rem[6][3];
 #pragma unroll
           for (int e = 0; e < 6; ++e) {
-            const unsigned b = rt[e];
+            const unsigned b = rtl[e];
             if (b == kRes3Ring) {
 #pragma unroll
               for (int c = 0; c < 3; ++c) rem[e][c] = f2(0.f, 0.f);
@@ -496,13 +511,9 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
               for (int c = 0; c < 3; ++c) rem[e][c] = col3_remote(b + 4u * (unsigned)(c * cstrV + rowoff));
             }
           }
-          float2 vk[SS][3], Hk[SS][3];
+          float2 Hk[SS][3];
 #pragma unroll
-          for (int k = 0; k < SS; ++k) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) vk[k][c] = lds2(src + c * cstrV + k * PV + rowoff);
-            yx_pass(k, vk[k], Hk[k]);
-          }
+          for (int k = 0; k < SS; ++k) yx_pass(k, vk[k], Hk[k]);
           auto val = [&](int z, int c) -> float2 { return z < 0 ? rem[z + 3][c] : (z < SS ? vk[z][c] : rem[z - SS + 3][c]); };
           float2 Fa[3], Fb[3], Fc[3];
 #pragma unroll
@@ -595,11 +606,12 @@ micro_fp32_3d_col_kernel(MicroArgs a, ResLaunch L) {
           else if (S == 2) stage_body(std::integral_constant<int, 2>{});
           else stage_body(std::integral_constant<int, 1>{});
         }
+        // arrive first: the warp's Kahan sum touches only its own shared-memory slots
+        if (cs > 1) cluster_arrive();
         if (stage == 1 && om != 0.f) {
           float part[3] = {part2[0].x + part2[0].y, part2[1].x + part2[1].y, part2[2].x + part2[2].y};
           warp_kahan_add(kah, lane, om, part);
         }
-        if (cs > 1) cluster_arrive();
       }
     }
     if (cs > 1) cluster_wait();   // pairs the last arrive
