@@ -55,7 +55,20 @@ def _source_hash(nvcc: str) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (unless the recorded source hash matches) and return the path of libhmm_gb300.so."""
+    """Compile (unless the recorded source hash matches) and return the path of libhmm_gb300.so.
+
+    Concurrent calls (test workers in parallel processes) are serialised by a lock
+    file beside the library: one compiles, the others then find the library current."""
+    import fcntl
+    with open(LIB + ".lock", "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     nvcc = _nvcc()
     digest = _source_hash(nvcc)
     if not force and os.path.exists(LIB) and os.path.exists(STAMP):
