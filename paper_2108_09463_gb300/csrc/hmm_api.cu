@@ -1043,6 +1043,7 @@ hmm_status hmm_micro_batch_points(void* handle, const double* M_dev, double* Hav
   if (!M_dev || !Havg_dev || (n_points > 0 && !points_host))
     return fail(h, HMM_ERR_INVALID_ARG, "null pointer");
   if (h->p.model != HMM_FIELD_MODEL) return fail(h, HMM_ERR_INVALID_ARG, "hmm_micro_batch_points needs a field-model handle");
+  h->wave_next = 0;   // like every other micro batch, it abandons a macro step in waves
   if (n_points < 0 || n_points > h->P) return fail(h, HMM_ERR_INVALID_ARG, "n_points must be 0..P");
   if (h->box_of_point.empty()) {
     h->box_of_point.assign(h->P, -1);
