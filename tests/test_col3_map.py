@@ -1,4 +1,4 @@
-"""The z-column 3D kernel's thread map (host logic, no GPU).
+"""The z-column 3D kernel's thread map and shared-memory accesses (host logic, no GPU).
 
 The kernel (csrc/micro_fp32_3d_col.cuh) stores each z-plane with a row stride of
 LD floats and gives thread t the tile (row y, column pair j) such that the 16
@@ -64,3 +64,35 @@ def test_column_kernel_thread_map():
             assert len(banks) == len(set(banks))
     # the 32^3 box: 338 tiles in 22 half-warps (352 threads), planes of 38-float rows
     assert _layout(32) == (38, 22)
+
+
+def test_column_kernel_plane_reads_and_thread_order_arrays():
+    """Every shared-memory access of the time loop stays inside its array. Thread t with
+    tile (y, j) works at box row yb = 3 + y and box column xb0 = 3 + 2j, stored at plane
+    offset rowoff = yb LD + xb0 + 1 (column x at offset x + 1): the y direction reads
+    rowoff + m LD (+1) for m = -3 .. 3, the x direction rowoff - 4 .. rowoff + 5 on its
+    own row; each of the kCol3S planes of a state array is one N x LD block. The
+    per-thread arrays (m_init, H(m_init), H(W), the state's carry) are indexed by plane
+    and thread, (k NT + t) 2 + h, inside kCol3S NT 2 floats per component."""
+    S_MAX = 3
+    for N in range(8, 33):
+        LD, halfwarps = _layout(N)
+        Ni, L = N - 6, LD // 2
+        NT = (16 * halfwarps + 31) // 32 * 32
+        PV = N * LD
+        for t in range(NT):
+            tile = _tile(t, Ni, L)
+            if tile is None:
+                continue
+            y, j = tile
+            yb, xb0 = 3 + y, 3 + 2 * j
+            rowoff = yb * LD + xb0 + 1
+            offs = [rowoff + m * LD + e for m in range(-3, 4) for e in (0, 1)]
+            offs += [rowoff + e for e in range(-4, 6)]
+            assert min(offs) >= 0 and max(offs) < PV, (N, t, tile)
+            # the stores of the tile's own nodes stay in the interior rows and inside the row
+            assert 3 <= yb <= N - 4 and xb0 + 2 < LD
+            for k in range(S_MAX):
+                for h in (0, 1):
+                    io = (k * NT + t) * 2 + h
+                    assert 0 <= io < S_MAX * NT * 2
