@@ -702,7 +702,9 @@ def run_reference(args, rank, world):
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOADS[name]["desc"], "name": name,
-                                        "precision": "fp64 oracle"},
+                                        "precision": "fp64 oracle",
+                                        "step": f"a bounded sample of the workload: {workers * args.ref_boxes_per_worker} "
+                                                "whole micro boxes (all micro steps), one per worker"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
