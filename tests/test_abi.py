@@ -169,3 +169,18 @@ def test_dns_null_arguments(lib):
     assert lib.hmm_dns_step(None, None, 1) == 7
     assert lib.hmm_dns_reset(None) == 7
     lib.hmm_dns_destroy(None)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c++", "c++17")])
+def test_headers_compile_on_their_own(tmp_path, lang, std):
+    """The public headers are plain C (no CUDA or torch types) and compile as C99 and C++17."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "use_headers.c"
+    src.write_text('#include "hmm.h"\n#include "hmm_dns.h"\nint main(void) { return (int)HMM_OK; }\n')
+    r = subprocess.run([cc, "-x", lang, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
