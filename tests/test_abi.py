@@ -184,3 +184,39 @@ def test_headers_compile_on_their_own(tmp_path, lang, std):
     r = subprocess.run([cc, "-x", lang, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_and_gets_a_host_side_refusal(tmp_path, lib):
+    """A C program (no Python) links libhmm_gb300.so, fills hmm_params with an invalid
+    dimension and gets HMM_ERR_INVALID_ARG with a message from hmm_last_error(NULL):
+    parameter validation runs on the host, before any CUDA call."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    from paper_2108_09463_gb300 import build
+    libdir = os.path.dirname(build())
+    src = tmp_path / "refusal.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "hmm.h"
+int main(void) {
+  hmm_params p;
+  void* h = NULL;
+  memset(&p, 0, sizeof p);
+  p.dim = 7;
+  hmm_status s = hmm_init(&p, NULL, &h);
+  printf("%d|%s\n", (int)s, hmm_last_error(NULL));
+  return s == HMM_ERR_INVALID_ARG && h == NULL ? 0 : 1;
+}
+''')
+    exe = tmp_path / "refusal"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", libdir, "-lhmm_gb300", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    status, msg = r.stdout.strip().split("|", 1)
+    assert int(status) == 1 and "dim" in msg
