@@ -14,7 +14,8 @@
   remaining error E_eps of the (EX2) micro problem falls by about four when eps is
   halved (E_eps <= C eps^2), with A^H from the cell problem; on the averaging
   width mu (Section 4.4, averaging domain size): steep while mu is a few eps, flat
-  from about 3.5 eps; and on the averaging time eta: steep while eta is a few eps^2.
+  from about 3.5 eps; on the averaging time eta: steep while eta is a few eps^2; and on
+  the box half-width mu': falling until the boundary error is below the rest.
 """
 import functools
 
@@ -267,3 +268,14 @@ def test_ex2_error_against_averaging_time():
     e05, e10, e15 = (_ex2_error(100, 3.9, 8, 10.0, eta) for eta in (0.5, 1.0, 1.5))
     assert e05 > 10 * e10 and e10 > 5 * e15, (e05, e10, e15)
     assert e15 < 2e-4
+
+
+def test_ex2_error_against_box_size():
+    """(EX2), eps = 1/100, mu = 3.9 eps, eta = 2 eps^2: E_avg against the half-width mu'
+    of the computational box (Section 4.4, full domain size): with mu' only a little
+    above mu the boundary error dominates, and it falls as mu' grows until the other
+    terms remain: measured 2.1e-2, 2.2e-3, 1.3e-4, 5.3e-5 and 5.3e-5 at mu' = 6, 8, 10,
+    12 and 14 eps (the paper has no model for this term; the pin is the fall).
+    """
+    e6, e8, e12 = (_ex2_error(100, 3.9, 8, mup, 2.0) for mup in (6.0, 8.0, 12.0))
+    assert e6 > 5 * e8 > 5 * 5 * e12, (e6, e8, e12)
